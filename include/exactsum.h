@@ -1,0 +1,169 @@
+/*
+ * exactsum.h -- C ABI of the GB300 exact floating-point summation library.
+ *
+ * The library computes the exact sum of n IEEE floating-point values and
+ * rounds it once, following Goodrich & Eldawy, "Parallel Algorithms for
+ * Summing Floating-Point Numbers" (arXiv:1605.05436):
+ *
+ *   - the problem (Section 1): given X = {x_1..x_n}, return S_n*, a
+ *     faithful rounding of S_n = sum x_i.  This library returns the
+ *     correctly rounded value (round to nearest, ties to even, by default),
+ *     which is always faithful, or a directed rounding on request;
+ *   - the method (Sections 2, 3 and 5): convert each element into digits of
+ *     a carry-free (alpha, beta)-regularised superaccumulator (Section 2,
+ *     Lemma 1), add the digits without propagating carries, merge the
+ *     partial accumulators carry-free, then propagate the signed carries
+ *     once and round from the most significant non-zero digit (Section 3,
+ *     steps 6-7; Section 5, steps 4-5).  The whole accumulator stays in
+ *     on-chip memory and the input is streamed once (Section 5, Theorem 5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Element types: EXACTSUM_F64 (IEEE binary64), EXACTSUM_F32 (binary32),
+ *    EXACTSUM_BF16 (bfloat16).  Arrays hold the raw IEEE bit patterns in
+ *    the machine's (little-endian) order and must be aligned to their
+ *    element size.  Subnormals are exact inputs.
+ *  - Any input format may be rounded to any output format; the exact sum
+ *    is rounded once, directly to the output format (no double rounding).
+ *  - Special values (the paper is silent; these are the library's rules):
+ *      any NaN, or both +Inf and -Inf present -> the quiet NaN of the output
+ *        format with sign +, payload not preserved;
+ *      otherwise any +Inf -> +Inf; otherwise any -Inf -> -Inf;
+ *      otherwise the exact finite sum is rounded; overflow follows IEEE 754
+ *        for the mode (to nearest -> Inf; toward zero -> max finite; up and
+ *        down -> Inf on their side, max finite on the other).
+ *  - Signed zero: an empty input gives +0.  If the exact sum is zero and
+ *    n >= 1: all inputs -0 -> -0; all inputs +0 -> +0; otherwise -0 under
+ *    EXACTSUM_RDOWN and +0 under the other modes (IEEE 754 rules for x + y).
+ *  - Device pointers (prefix d_) are CUDA device memory owned by the
+ *    caller; host pointers (prefix h_) are host memory owned by the caller
+ *    (page-locked memory gives full copy bandwidth).  The library never
+ *    frees caller memory.
+ *  - Asynchrony: entry points that take a stream enqueue work on it and
+ *    return without waiting, unless stated otherwise.  Results in device
+ *    memory are valid once the stream has reached the call.
+ *  - A handle (exactsum_t) owns device workspace.  Work enqueued through one
+ *    handle must not overlap in time on the GPU: issue it on one stream, or
+ *    order the streams.  Use one handle per concurrent stream.  A handle is
+ *    not thread-safe; lock it or give each host thread its own.
+ *  - Errors: every entry point returns an exactsum_status; no exception or
+ *    abort crosses the ABI.  Arguments are checked on the host before any
+ *    work is enqueued: a non-OK return means nothing was enqueued (except
+ *    EXACTSUM_ECUDA, which reports a CUDA error from the launch or copy).
+ *    exactsum_last_error() gives a message for the last failure.
+ *  - Limits: n < 2^48 elements per call.
+ */
+#ifndef EXACTSUM_H
+#define EXACTSUM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+/* A CUDA stream handle (the same type as cudaStream_t); NULL is the legacy
+ * default stream. */
+typedef struct CUstream_st* exactsum_stream_t;
+
+typedef struct exactsum_ctx* exactsum_t;
+
+typedef enum { EXACTSUM_F64 = 0, EXACTSUM_F32 = 1, EXACTSUM_BF16 = 2 } exactsum_dtype;
+
+typedef enum {
+    EXACTSUM_RNE = 0,   /* to nearest, ties to even */
+    EXACTSUM_RTZ = 1,   /* toward zero */
+    EXACTSUM_RUP = 2,   /* toward +infinity */
+    EXACTSUM_RDOWN = 3  /* toward -infinity */
+} exactsum_round;
+
+typedef enum {
+    EXACTSUM_OK = 0,
+    EXACTSUM_EINVAL = 1,       /* bad argument (null, negative size, unknown enum,
+                                  misaligned pointer, size over the limit) */
+    EXACTSUM_ENOMEM = 2,       /* device or host allocation failed */
+    EXACTSUM_ECUDA = 3,        /* a CUDA call failed; see exactsum_last_error */
+    EXACTSUM_ETIMEOUT = 4,     /* a bounded wait gave up */
+    EXACTSUM_EUNSUPPORTED = 5  /* device is not sm_103 */
+} exactsum_status;
+
+/* Words of an accumulator (see exactsum_acc_*): 72 signed 64-bit digits in
+ * radix 2^32 (digit i weighs 2^(32 i) units of the input format's smallest
+ * subnormal), then 5 counters (NaN seen, +Inf seen, -Inf seen, an element
+ * other than +0 seen, an element other than -0 seen), then the element
+ * count, then 2 reserved words.  Two accumulators of the same input format
+ * merge by adding them word by word (Lemma 1: digit sums stay exact and
+ * carries are deferred), so they can be summed across streams, devices or
+ * processes with any integer all-reduce. */
+#define EXACTSUM_ACC_DIGITS 72
+#define EXACTSUM_ACC_WORDS 80
+#define EXACTSUM_ACC_BYTES (EXACTSUM_ACC_WORDS * 8)
+
+/* ---------------------------------------------------------------------- */
+/* Handle                                                                  */
+/* ---------------------------------------------------------------------- */
+
+/* Create a handle on CUDA device `device` (which becomes current on the
+ * calling thread) and allocate its workspace.  `max_segments_hint` sizes
+ * the segmented-sum workspace up front (0: grow on first use; growth
+ * happens outside any stream capture).  On success *out receives the
+ * handle.  Fails with EXACTSUM_EUNSUPPORTED on a device that is not
+ * compute capability 10.3. */
+exactsum_status exactsum_create(exactsum_t* out, int device, int64_t max_segments_hint);
+
+/* Free the handle's workspace (after synchronising its device). NULL is OK. */
+exactsum_status exactsum_destroy(exactsum_t h);
+
+/* Message for the last failing call on `h` (or on a NULL handle); never
+ * NULL; valid until the next call on the same handle. */
+const char* exactsum_last_error(exactsum_t h);
+
+/* ---------------------------------------------------------------------- */
+/* Single array (Section 5 Theorem 5 shape: stream once, accumulator on    */
+/* chip; Section 6.1 shape: each CTA a reducer, one post-process)          */
+/* ---------------------------------------------------------------------- */
+
+/* d_result (one element of out_dtype, device) <- round(sum of d_x[0..n)).
+ * d_x: n elements of in_dtype in device memory (may be NULL when n == 0).
+ * One kernel launch; no host synchronisation. */
+exactsum_status exactsum_sum(exactsum_t h, const void* d_x, int64_t n, int in_dtype,
+                             int out_dtype, int mode, void* d_result, exactsum_stream_t stream);
+
+/* End-to-end variant with host buffers: copies h_x to the device in
+ * pipelined chunks on `stream`, sums it, copies the rounded result to
+ * h_result (one element of out_dtype), and waits for the stream.  The
+ * device copy buffers belong to the handle. */
+exactsum_status exactsum_sum_host(exactsum_t h, const void* h_x, int64_t n, int in_dtype,
+                                  int out_dtype, int mode, void* h_result,
+                                  exactsum_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Accumulators: exact partial sums that persist between calls             */
+/* (Section 2: superaccumulator addition; Section 6.1: reducers write      */
+/* partial accumulators that a post-process merges and rounds)             */
+/* ---------------------------------------------------------------------- */
+
+/* Set the EXACTSUM_ACC_WORDS words at d_acc (device, 8-byte aligned) to
+ * zero (the empty sum). */
+exactsum_status exactsum_acc_zero(exactsum_t h, void* d_acc, exactsum_stream_t stream);
+
+/* d_acc += exact sum of d_x[0..n) (in_dtype).  All adds into one
+ * accumulator must use the same in_dtype.  The digits are regularised
+ * after each call (|digit| <= 2^32), so up to 2^30 accumulators can be
+ * merged by plain addition. */
+exactsum_status exactsum_acc_add(exactsum_t h, const void* d_x, int64_t n, int in_dtype,
+                                 void* d_acc, exactsum_stream_t stream);
+
+/* d_result (one element of out_dtype) <- round(value of d_acc), where d_acc
+ * holds sums of in_dtype elements.  d_acc is not modified. */
+exactsum_status exactsum_acc_round(exactsum_t h, const void* d_acc, int in_dtype,
+                                   int out_dtype, int mode, void* d_result,
+                                   exactsum_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXACTSUM_H */

@@ -1,0 +1,240 @@
+"""GB300 exact floating-point summation.
+
+Goodrich & Eldawy, "Parallel Algorithms for Summing Floating-Point Numbers"
+(arXiv:1605.05436): reduce n IEEE values to their exact sum in a carry-free
+superaccumulator, then round once.
+
+This module is the thin Python binding of ``libexactsum.so`` (the C ABI in
+``include/exactsum.h``).  The functions named ``exactsum_*`` mirror the C
+entry points one to one and only marshal arguments; every step of the
+summation runs in the library's CUDA kernels.  The torch helpers at the end
+(``exact_sum`` and friends) take tensors, pass their device pointers and the
+current CUDA stream, and allocate result tensors -- PyTorch supplies memory
+and streams only.
+
+There is no CPU fallback: if the library is not built, or no sm_103 GPU is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libexactsum.so")
+
+F64, F32, BF16 = 0, 1, 2
+RNE, RTZ, RUP, RDOWN = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
+ACC_WORDS = 80
+ACC_BYTES = 8 * ACC_WORDS
+ITEMSIZE = {F64: 8, F32: 4, BF16: 2}
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+# name -> (argtypes); every entry point returns an int status except
+# exactsum_last_error.
+_SIGNATURES = {
+    "exactsum_create": [ctypes.POINTER(_vp), _int, _i64],
+    "exactsum_destroy": [_vp],
+    "exactsum_sum": [_vp, _vp, _i64, _int, _int, _int, _vp, _vp],
+    "exactsum_sum_host": [_vp, _vp, _i64, _int, _int, _int, _vp, _vp],
+    "exactsum_acc_zero": [_vp, _vp, _vp],
+    "exactsum_acc_add": [_vp, _vp, _i64, _int, _vp, _vp],
+    "exactsum_acc_round": [_vp, _vp, _int, _int, _int, _vp, _vp],
+}
+OPTIONAL_SIGNATURES: dict = {}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ExactSumError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"exactsum status {status}: {message}")
+        self.status = status
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+    from . import buildlib as _b
+    return _b.build(force=force, verbose=verbose)
+
+
+def library() -> ctypes.CDLL:
+    """Load ``libexactsum.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                                   "(paper_1605_05436_gb300.build())")
+            # load the CUDA runtime through torch first when available, so that
+            # the library and torch share one runtime instance
+            try:
+                import torch  # noqa: F401
+            except ImportError:
+                pass
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, argtypes in {**_SIGNATURES, **OPTIONAL_SIGNATURES}.items():
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    if name in _SIGNATURES:
+                        raise RuntimeError(f"{LIB_PATH} does not export {name}")
+                    continue
+                fn.argtypes = argtypes
+                fn.restype = _int
+            lib.exactsum_last_error.argtypes = [_vp]
+            lib.exactsum_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, handle) -> None:
+    if status != OK:
+        msg = library().exactsum_last_error(handle)
+        raise ExactSumError(status, msg.decode(errors="replace") if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# C entry points (same names and argument order as include/exactsum.h)
+# ---------------------------------------------------------------------------
+
+def exactsum_create(device: int = 0, max_segments_hint: int = 0) -> int:
+    h = _vp()
+    _check(library().exactsum_create(ctypes.byref(h), device, max_segments_hint), None)
+    return h.value
+
+
+def exactsum_destroy(handle: int) -> None:
+    _check(library().exactsum_destroy(handle), handle)
+
+
+def exactsum_last_error(handle) -> str:
+    return library().exactsum_last_error(handle).decode(errors="replace")
+
+
+def exactsum_sum(handle, d_x, n, in_dtype, out_dtype, mode, d_result, stream) -> None:
+    _check(library().exactsum_sum(handle, d_x, n, in_dtype, out_dtype, mode, d_result, stream), handle)
+
+
+def exactsum_sum_host(handle, h_x, n, in_dtype, out_dtype, mode, h_result, stream) -> None:
+    _check(library().exactsum_sum_host(handle, h_x, n, in_dtype, out_dtype, mode, h_result, stream),
+           handle)
+
+
+def exactsum_acc_zero(handle, d_acc, stream) -> None:
+    _check(library().exactsum_acc_zero(handle, d_acc, stream), handle)
+
+
+def exactsum_acc_add(handle, d_x, n, in_dtype, d_acc, stream) -> None:
+    _check(library().exactsum_acc_add(handle, d_x, n, in_dtype, d_acc, stream), handle)
+
+
+def exactsum_acc_round(handle, d_acc, in_dtype, out_dtype, mode, d_result, stream) -> None:
+    _check(library().exactsum_acc_round(handle, d_acc, in_dtype, out_dtype, mode, d_result, stream),
+           handle)
+
+
+# ---------------------------------------------------------------------------
+# torch helpers (memory and streams only)
+# ---------------------------------------------------------------------------
+_handles: dict = {}
+
+
+def handle_for(device: int):
+    """A cached library handle for a CUDA device index."""
+    with _lock:
+        h = _handles.get(device)
+    if h is None:
+        h = exactsum_create(device, 0)
+        with _lock:
+            _handles[device] = h
+    return h
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    """Input format of a tensor: float64/float32/bfloat16, or raw IEEE bits
+    held in int64/uint64 (FP64), int32/uint32 (FP32), int16/uint16 (BF16)."""
+    torch = _torch()
+    m = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16,
+         torch.int64: F64, torch.int32: F32, torch.int16: BF16}
+    for name, code in (("uint64", F64), ("uint32", F32), ("uint16", BF16)):
+        if hasattr(torch, name):
+            m[getattr(torch, name)] = code
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def result_tensor(out_dtype: int, device, count: int = 1):
+    torch = _torch()
+    td = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}[out_dtype]
+    return torch.empty(count, dtype=td, device=device)
+
+
+def _stream_ptr(stream, device):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return s.cuda_stream
+
+
+def exact_sum(x, out_dtype: int | None = None, mode: int = RNE, stream=None, out=None):
+    """Exact sum of a contiguous CUDA tensor, rounded once; returns a
+    one-element tensor of the output format (float64/float32/bfloat16)."""
+    if not x.is_cuda:
+        raise ValueError("exact_sum takes a CUDA tensor (use exact_sum_host for host memory)")
+    if not x.is_contiguous():
+        raise ValueError("input must be contiguous")
+    in_dtype = dtype_code(x)
+    out_dtype = in_dtype if out_dtype is None else out_dtype
+    dev = x.device.index
+    if out is None:
+        out = result_tensor(out_dtype, x.device)
+    exactsum_sum(handle_for(dev), x.data_ptr() if x.numel() else None, x.numel(), in_dtype,
+                 out_dtype, mode, out.data_ptr(), _stream_ptr(stream, dev))
+    return out
+
+
+def exact_sum_host(x, out_dtype: int | None = None, mode: int = RNE, device: int = 0, stream=None):
+    """End to end from host memory (a CPU tensor, ideally pinned): returns the
+    result's raw bits as a Python int after the stream has finished."""
+    if x.is_cuda or not x.is_contiguous():
+        raise ValueError("exact_sum_host takes a contiguous CPU tensor")
+    in_dtype = dtype_code(x)
+    out_dtype = in_dtype if out_dtype is None else out_dtype
+    res = ctypes.c_uint64(0)
+    exactsum_sum_host(handle_for(device), x.data_ptr() if x.numel() else None, x.numel(), in_dtype,
+                      out_dtype, mode, ctypes.addressof(res), _stream_ptr(stream, device))
+    return res.value & ((1 << (8 * ITEMSIZE[out_dtype])) - 1)
+
+
+def new_accumulator(device):
+    """A zeroed device accumulator (EXACTSUM_ACC_WORDS int64 words)."""
+    torch = _torch()
+    return torch.zeros(ACC_WORDS, dtype=torch.int64, device=device)
+
+
+def acc_add(acc, x, stream=None):
+    in_dtype = dtype_code(x)
+    dev = x.device.index
+    exactsum_acc_add(handle_for(dev), x.data_ptr() if x.numel() else None, x.numel(), in_dtype,
+                     acc.data_ptr(), _stream_ptr(stream, dev))
+    return acc
+
+
+def acc_round(acc, in_dtype: int, out_dtype: int | None = None, mode: int = RNE, stream=None):
+    out_dtype = in_dtype if out_dtype is None else out_dtype
+    dev = acc.device.index
+    out = result_tensor(out_dtype, acc.device)
+    exactsum_acc_round(handle_for(dev), acc.data_ptr(), in_dtype, out_dtype, mode, out.data_ptr(),
+                       _stream_ptr(stream, dev))
+    return out

@@ -1,0 +1,223 @@
+// digits.cuh -- per-element conversion into superaccumulator digits and the
+// carry-free digit arithmetic of Section 2 (Lemma 1), for sm_103a.
+//
+// Representation.  Every input element is x = (-1)^s * m * 2^p * unit, where
+// for a finite input with biased exponent E and stored fraction F:
+//     m = F            if E == 0 (subnormal or zero), else F + 2^t,
+//     p = max(E, 1) - 1,
+// and unit is the format's smallest subnormal (2^-1074, 2^-149, 2^-133).
+// The running sum is kept as a vector of signed 64-bit digits D_i with
+// value sum_i D_i * 2^(r*i) * unit, where r is the digit radix in bits.  This
+// is the integer-digit form of the (alpha, beta)-regularised superaccumulator
+// (Section 2: y_i = Y_i R^i with integer Y_i, consecutive digits overlapping),
+// with R = 2^r and a much wider overlap than one bit: a digit may hold many
+// un-carried additions before it has to be regularised.
+//
+//   FP64:   r = 32.  m < 2^53 and p & 31 < 32, so m * 2^(p & 31) < 2^84
+//           splits into a low part < 2^32 (digit p >> 5) and a high part
+//           < 2^52 (digit (p >> 5) + 1): two digit additions per element.
+//           66 digits per thread (digit 65 only receives carries).
+//   FP32:   r = 8.   m < 2^24, so m * 2^(p & 7) < 2^31 goes into one digit
+//   BF16:            (p >> 3) without splitting.  33 digits per thread.
+//
+// Regularisation (Lemma 1, generalised to deferred carries): a digit D is
+// replaced by D - c * R and its upper neighbour gains c, with
+// c = floor((D + R/2) / R) (the balanced choice; Lemma 1 allows any signed
+// carry that brings the digit into range).  Carries only ever move to the
+// adjacent digit.
+#pragma once
+#include <cstdint>
+
+namespace es {
+
+enum : int { F64 = 0, F32 = 1, BF16 = 2 };
+enum : int { RNE = 0, RTZ = 1, RUP = 2, RDOWN = 3 };
+
+constexpr int ACC_DIGITS = 72;  // radix-2^32 digits of a merged accumulator
+constexpr int ACC_WORDS = 80;   // digits + 5 counters + count + 2 reserved
+constexpr int W_NAN = 72, W_PINF = 73, W_NINF = 74, W_NOTPZ = 75, W_NOTNZ = 76, W_COUNT = 77;
+
+// Per-thread accumulator geometry by input format.
+template <int DT> struct Geometry;
+template <> struct Geometry<F64> {
+  static constexpr int RADIX_BITS = 32;
+  static constexpr int DIGITS = 66;           // per-thread digits
+  static constexpr int ELEM_BYTES = 8;
+  static constexpr int REG_EVERY = 1024;      // adds between regularisations (< 2^11)
+  static constexpr uint32_t EXP_SPECIAL = 0x7FF;
+};
+template <> struct Geometry<F32> {
+  static constexpr int RADIX_BITS = 8;
+  static constexpr int DIGITS = 33;
+  static constexpr int ELEM_BYTES = 4;
+  static constexpr int REG_EVERY = 1 << 30;   // |add| < 2^31: int64 holds 2^32 of them
+  static constexpr uint32_t EXP_SPECIAL = 0xFF;
+};
+template <> struct Geometry<BF16> {
+  static constexpr int RADIX_BITS = 8;
+  static constexpr int DIGITS = 33;
+  static constexpr int ELEM_BYTES = 2;
+  static constexpr int REG_EVERY = 1 << 30;
+  static constexpr uint32_t EXP_SPECIAL = 0xFF;
+};
+
+__host__ __device__ constexpr int unit_exp_of(int dt) {
+  return dt == F64 ? -1074 : (dt == F32 ? -149 : -133);
+}
+
+// ---------------------------------------------------------------------------
+// Per-element conversion and digit addition (Section 3 step 2 / Section 5
+// step 1: split each element into O(1) components at radix-aligned
+// exponents; Section 5 Theorem 5: add them into the resident accumulator in
+// any order).  `col` points at this thread's digit 0; digit i lives at
+// col[i * STRIDE] (digit-major, thread-minor: conflict-free shared banks).
+// `emax` tracks the largest biased exponent seen, which flags specials
+// (E all ones) and all-zero/subnormal inputs for a later exact rescan.
+// ---------------------------------------------------------------------------
+template <int STRIDE>
+__device__ __forceinline__ void add_f64(int64_t* __restrict__ col, uint32_t lo, uint32_t hi,
+                                        uint32_t& emax) {
+  const uint32_t E = (hi >> 20) & 0x7FFu;
+  emax = max(emax, E);
+  const uint32_t mhi = (hi & 0xFFFFFu) | (E != 0u ? 0x100000u : 0u);  // bits 32..52 of m
+  const uint32_t p = max(E, 1u) - 1u;
+  // v = m << (p & 31) as three 32-bit words w2:w1:w0 (funnel shifts use p & 31)
+  const uint32_t w0 = __funnelshift_l(0u, lo, p);
+  const uint32_t w1 = __funnelshift_l(lo, mhi, p);
+  const uint32_t w2 = __funnelshift_l(mhi, 0u, p);
+  const int64_t s = (int64_t)((int32_t)hi >> 31);  // 0 or -1
+  const int64_t vlo = ((int64_t)w0 ^ s) - s;
+  const int64_t vhi = ((int64_t)(((uint64_t)w2 << 32) | w1) ^ s) - s;
+  int64_t* d = col + (p >> 5) * STRIDE;
+  d[0] += vlo;
+  d[STRIDE] += vhi;
+}
+
+template <int STRIDE>
+__device__ __forceinline__ void add_f32(int64_t* __restrict__ col, uint32_t w, uint32_t& emax) {
+  const uint32_t E = (w >> 23) & 0xFFu;
+  emax = max(emax, E);
+  const uint32_t m = (w & 0x7FFFFFu) | (E != 0u ? 0x800000u : 0u);
+  const uint32_t p = max(E, 1u) - 1u;
+  const int32_t s = (int32_t)w >> 31;
+  const int32_t v = ((int32_t)(m << (p & 7u)) ^ s) - s;  // |v| < 2^31
+  col[(p >> 3) * STRIDE] += (int64_t)v;
+}
+
+template <int STRIDE>
+__device__ __forceinline__ void add_bf16(int64_t* __restrict__ col, uint32_t h, uint32_t& emax) {
+  const uint32_t E = (h >> 7) & 0xFFu;
+  emax = max(emax, E);
+  const uint32_t m = (h & 0x7Fu) | (E != 0u ? 0x80u : 0u);
+  const uint32_t p = max(E, 1u) - 1u;
+  const int32_t s = -(int32_t)((h >> 15) & 1u);
+  const int32_t v = ((int32_t)(m << (p & 7u)) ^ s) - s;  // |v| < 2^15
+  col[(p >> 3) * STRIDE] += (int64_t)v;
+}
+
+// Add all elements held in one 16-byte vector.
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_vec(int64_t* __restrict__ col, const uint4& v, uint32_t& emax) {
+  if constexpr (DT == F64) {
+    add_f64<STRIDE>(col, v.x, v.y, emax);
+    add_f64<STRIDE>(col, v.z, v.w, emax);
+  } else if constexpr (DT == F32) {
+    add_f32<STRIDE>(col, v.x, emax);
+    add_f32<STRIDE>(col, v.y, emax);
+    add_f32<STRIDE>(col, v.z, emax);
+    add_f32<STRIDE>(col, v.w, emax);
+  } else {
+    add_bf16<STRIDE>(col, v.x & 0xFFFFu, emax);
+    add_bf16<STRIDE>(col, v.x >> 16, emax);
+    add_bf16<STRIDE>(col, v.y & 0xFFFFu, emax);
+    add_bf16<STRIDE>(col, v.y >> 16, emax);
+    add_bf16<STRIDE>(col, v.z & 0xFFFFu, emax);
+    add_bf16<STRIDE>(col, v.z >> 16, emax);
+    add_bf16<STRIDE>(col, v.w & 0xFFFFu, emax);
+    add_bf16<STRIDE>(col, v.w >> 16, emax);
+  }
+}
+
+// Add one element given by its raw bits (for unaligned heads and tails).
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_one(int64_t* __restrict__ col, uint64_t bits, uint32_t& emax) {
+  if constexpr (DT == F64) add_f64<STRIDE>(col, (uint32_t)bits, (uint32_t)(bits >> 32), emax);
+  else if constexpr (DT == F32) add_f32<STRIDE>(col, (uint32_t)bits, emax);
+  else add_bf16<STRIDE>(col, (uint32_t)bits, emax);
+}
+
+template <int DT>
+__device__ __forceinline__ uint64_t load_one(const void* x, int64_t i) {
+  if constexpr (DT == F64) return __ldg((const unsigned long long*)x + i);
+  else if constexpr (DT == F32) return __ldg((const unsigned int*)x + i);
+  else return __ldg((const unsigned short*)x + i);
+}
+
+// Regularise one thread's digits in place: afterwards |D_i| <= R/2 for all
+// but the top digit, which absorbs the last carry.
+template <int DT, int STRIDE>
+__device__ __forceinline__ void regularise(int64_t* __restrict__ col) {
+  constexpr int RB = Geometry<DT>::RADIX_BITS;
+  constexpr int ND = Geometry<DT>::DIGITS;
+  int64_t carry = 0;
+#pragma unroll 4
+  for (int i = 0; i < ND - 1; ++i) {
+    const int64_t v = col[i * STRIDE] + carry;
+    const int64_t c = (v + ((int64_t)1 << (RB - 1))) >> RB;
+    col[i * STRIDE] = v - (c << RB);
+    carry = c;
+  }
+  col[(ND - 1) * STRIDE] += carry;
+}
+
+// Value of radix-2^32 digit i contributed by one thread's (regularised)
+// digits: for FP64 it is digit i itself; for the radix-2^8 formats it
+// gathers digits 4i .. 4i+3.
+template <int DT, int STRIDE>
+__device__ __forceinline__ int64_t digit32(const int64_t* __restrict__ col, int i) {
+  constexpr int ND = Geometry<DT>::DIGITS;
+  if constexpr (DT == F64) {
+    return i < ND ? col[i * STRIDE] : 0;
+  } else {
+    int64_t v = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int j = 4 * i + k;
+      if (j < ND) v += col[j * STRIDE] * ((int64_t)1 << (8 * k));
+    }
+    return v;
+  }
+}
+
+// Classify one element for the special-value and signed-zero counters.
+// flags bit 0: NaN, bit 1: +Inf, bit 2: -Inf, bit 3: not +0, bit 4: not -0.
+template <int DT>
+__device__ __forceinline__ uint32_t classify(uint64_t bits) {
+  constexpr int W = Geometry<DT>::ELEM_BYTES * 8;
+  constexpr int FB = DT == F64 ? 52 : (DT == F32 ? 23 : 7);
+  constexpr uint64_t SIGN = (uint64_t)1 << (W - 1);
+  constexpr uint64_t EXPM = (uint64_t)Geometry<DT>::EXP_SPECIAL << FB;
+  constexpr uint64_t FRACM = ((uint64_t)1 << FB) - 1;
+  uint32_t f = 0;
+  if ((bits & EXPM) == EXPM) {
+    if (bits & FRACM) f |= 1u;
+    else f |= (bits & SIGN) ? 4u : 2u;
+  }
+  if (bits != 0) f |= 8u;
+  if (bits != SIGN) f |= 16u;
+  return f;
+}
+
+// Regularise a 72-digit radix-2^32 accumulator in place (one thread).
+__device__ __forceinline__ void regularise72(int64_t* d) {
+  int64_t carry = 0;
+  for (int i = 0; i < ACC_DIGITS - 1; ++i) {
+    const int64_t v = d[i] + carry;
+    const int64_t c = (v + ((int64_t)1 << 31)) >> 32;
+    d[i] = v - (c << 32);
+    carry = c;
+  }
+  d[ACC_DIGITS - 1] += carry;
+}
+
+}  // namespace es

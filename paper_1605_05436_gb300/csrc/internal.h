@@ -1,0 +1,28 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace es {
+
+// Arguments of the single-array sum kernel.
+struct SumArgs {
+  const void* x;       // input (element-aligned)
+  int64_t n;           // elements
+  int64_t head;        // elements before the first 16-byte boundary (CTA 0)
+  int64_t nvec;        // 16-byte vectors after the head
+  int64_t tail;        // elements after the vectors (last CTA)
+  int out, mode;       // output format and rounding mode
+  void* result;        // result element (result mode)
+  int64_t* acc;        // accumulator to add into (accumulate mode), or null
+  int64_t* partials;   // grid x ACC_WORDS scratch
+  unsigned int* ticket;  // zero between launches; reset by the last CTA
+};
+
+cudaError_t launch_sum(int in_dt, const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out);
+cudaError_t launch_round_acc(const int64_t* acc, int in_dt, int out, int mode, void* result,
+                             cudaStream_t stream);
+int sum_threads_per_cta(int in_dt);
+
+}  // namespace es
