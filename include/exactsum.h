@@ -162,6 +162,62 @@ exactsum_status exactsum_acc_round(exactsum_t h, const void* d_acc, int in_dtype
                                    int out_dtype, int mode, void* d_result,
                                    exactsum_stream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* Segmented (batched) sums: one launch for many CSR segments              */
+/* (Section 6.1 MapReduce: tiles of the input are mapped to reducers,       */
+/* each reducer builds an accumulator, per-key accumulators are merged     */
+/* carry-free and rounded once)                                            */
+/* ---------------------------------------------------------------------- */
+
+/* Device status bits reported by exactsum_device_status. */
+#define EXACTSUM_STATUS_BAD_OFFSETS 1  /* a segment had offsets[s+1] < offsets[s] or offsets[s] < 0 */
+#define EXACTSUM_STATUS_MAP_OVERFLOW 2 /* more tiles than the tile map holds (input larger than HBM) */
+
+/* d_results[s] <- round(sum of d_x[d_offsets[s] .. d_offsets[s+1])) for
+ * s in [0, num_segments).
+ *   d_offsets: num_segments + 1 int64 CSR offsets in device memory (any
+ *     non-decreasing, non-negative sequence; offsets[0] need not be 0).
+ *   d_results: num_segments elements of out_dtype in device memory.
+ * Empty segments give +0.  Segments with invalid offsets give a quiet NaN
+ * and set EXACTSUM_STATUS_BAD_OFFSETS in the handle's device status word.
+ * The work (a small planning pass plus one persistent reducer kernel) is
+ * captured into a CUDA graph on first use of each (pointers, sizes, types,
+ * configuration) signature and replayed afterwards; when `stream` is being
+ * captured by the caller the kernels are launched into that capture instead.
+ * The reducer configuration comes from the autotuner's table (see
+ * exactsum_segmented_autotune) for this input format and size class
+ * (ceil(log2 num_segments)), else a default.  Workspace grows on demand
+ * (never during a capture); num_segments < 2^31. */
+exactsum_status exactsum_segmented_sum(exactsum_t h, const void* d_x, const int64_t* d_offsets,
+                                       int64_t num_segments, int in_dtype, int out_dtype, int mode,
+                                       void* d_results, exactsum_stream_t stream);
+
+/* The one-launch-per-segment form of the same computation: h_offsets are
+ * in host memory and every segment is summed by its own exactsum_sum call.
+ * Same results bit for bit; kept as the baseline the batched call is
+ * measured against. */
+exactsum_status exactsum_sum_each(exactsum_t h, const void* d_x, const int64_t* h_offsets,
+                                  int64_t num_segments, int in_dtype, int out_dtype, int mode,
+                                  void* d_results, exactsum_stream_t stream);
+
+/* Autotuner (synchronous): times each reducer configuration (two CTA
+ * sizes x three tile sizes) on this very input, keeps the fastest for the
+ * input format and size class, and reports it through the non-NULL output
+ * pointers.  d_results_scratch: num_segments elements of in_dtype. */
+exactsum_status exactsum_segmented_autotune(exactsum_t h, const void* d_x, const int64_t* d_offsets,
+                                            int64_t num_segments, int in_dtype,
+                                            void* d_results_scratch, exactsum_stream_t stream,
+                                            int* best_warps, int64_t* best_tile, float* best_ms);
+
+/* Save / load the autotuner's table as JSON
+ * ({"segmented": [{"in_dtype", "log2_segments", "warps", "tile", "ms"}...]}). */
+exactsum_status exactsum_tuning_save(exactsum_t h, const char* path);
+exactsum_status exactsum_tuning_load(exactsum_t h, const char* path);
+
+/* Synchronise the handle's device, return the accumulated device status
+ * bits (EXACTSUM_STATUS_*) in *status_out and clear them. */
+exactsum_status exactsum_device_status(exactsum_t h, int64_t* status_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,13 @@ _SIGNATURES = {
     "exactsum_acc_zero": [_vp, _vp, _vp],
     "exactsum_acc_add": [_vp, _vp, _i64, _int, _vp, _vp],
     "exactsum_acc_round": [_vp, _vp, _int, _int, _int, _vp, _vp],
+    "exactsum_segmented_sum": [_vp, _vp, _vp, _i64, _int, _int, _int, _vp, _vp],
+    "exactsum_sum_each": [_vp, _vp, _vp, _i64, _int, _int, _int, _vp, _vp],
+    "exactsum_segmented_autotune": [_vp, _vp, _vp, _i64, _int, _vp, _vp, ctypes.POINTER(_int),
+                                    ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_float)],
+    "exactsum_tuning_save": [_vp, ctypes.c_char_p],
+    "exactsum_tuning_load": [_vp, ctypes.c_char_p],
+    "exactsum_device_status": [_vp, ctypes.POINTER(_i64)],
 }
 OPTIONAL_SIGNATURES: dict = {}
 
@@ -137,6 +144,45 @@ def exactsum_acc_add(handle, d_x, n, in_dtype, d_acc, stream) -> None:
 def exactsum_acc_round(handle, d_acc, in_dtype, out_dtype, mode, d_result, stream) -> None:
     _check(library().exactsum_acc_round(handle, d_acc, in_dtype, out_dtype, mode, d_result, stream),
            handle)
+
+
+def exactsum_segmented_sum(handle, d_x, d_offsets, num_segments, in_dtype, out_dtype, mode, d_results,
+                           stream) -> None:
+    _check(library().exactsum_segmented_sum(handle, d_x, d_offsets, num_segments, in_dtype, out_dtype,
+                                            mode, d_results, stream), handle)
+
+
+def exactsum_sum_each(handle, d_x, h_offsets, num_segments, in_dtype, out_dtype, mode, d_results,
+                      stream) -> None:
+    _check(library().exactsum_sum_each(handle, d_x, h_offsets, num_segments, in_dtype, out_dtype, mode,
+                                       d_results, stream), handle)
+
+
+def exactsum_segmented_autotune(handle, d_x, d_offsets, num_segments, in_dtype, d_results_scratch,
+                                stream):
+    """Returns (warps, tile, ms) of the fastest reducer configuration."""
+    w, t, ms = _int(0), _i64(0), ctypes.c_float(0)
+    _check(library().exactsum_segmented_autotune(handle, d_x, d_offsets, num_segments, in_dtype,
+                                                 d_results_scratch, stream, ctypes.byref(w),
+                                                 ctypes.byref(t), ctypes.byref(ms)), handle)
+    return w.value, t.value, ms.value
+
+
+def exactsum_tuning_save(handle, path: str) -> None:
+    _check(library().exactsum_tuning_save(handle, path.encode()), handle)
+
+
+def exactsum_tuning_load(handle, path: str) -> None:
+    _check(library().exactsum_tuning_load(handle, path.encode()), handle)
+
+
+def exactsum_device_status(handle) -> int:
+    v = _i64(0)
+    _check(library().exactsum_device_status(handle, ctypes.byref(v)), handle)
+    return v.value
+
+
+STATUS_BAD_OFFSETS, STATUS_MAP_OVERFLOW = 1, 2
 
 
 # ---------------------------------------------------------------------------
@@ -237,4 +283,39 @@ def acc_round(acc, in_dtype: int, out_dtype: int | None = None, mode: int = RNE,
     out = result_tensor(out_dtype, acc.device)
     exactsum_acc_round(handle_for(dev), acc.data_ptr(), in_dtype, out_dtype, mode, out.data_ptr(),
                        _stream_ptr(stream, dev))
+    return out
+
+
+def segmented_sum(x, offsets, out_dtype: int | None = None, mode: int = RNE, stream=None, out=None):
+    """Exact sums of CSR segments: ``offsets`` is an int64 CUDA tensor of
+    S + 1 entries; returns S results of the output format."""
+    if not (x.is_cuda and offsets.is_cuda):
+        raise ValueError("segmented_sum takes CUDA tensors")
+    torch = _torch()
+    if offsets.dtype != torch.int64 or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous int64 tensor")
+    in_dtype = dtype_code(x)
+    out_dtype = in_dtype if out_dtype is None else out_dtype
+    S = offsets.numel() - 1
+    dev = x.device.index
+    if out is None:
+        out = result_tensor(out_dtype, x.device, max(S, 0))
+    exactsum_segmented_sum(handle_for(dev), x.data_ptr() if x.numel() else None, offsets.data_ptr(), S,
+                           in_dtype, out_dtype, mode, out.data_ptr() if S > 0 else None,
+                           _stream_ptr(stream, dev))
+    return out
+
+
+def sum_each(x, offsets_host, out_dtype: int | None = None, mode: int = RNE, stream=None, out=None):
+    """One exactsum_sum launch per segment (host int64 offsets): the baseline."""
+    torch = _torch()
+    off = offsets_host.to(torch.int64).contiguous()
+    in_dtype = dtype_code(x)
+    out_dtype = in_dtype if out_dtype is None else out_dtype
+    S = off.numel() - 1
+    dev = x.device.index
+    if out is None:
+        out = result_tensor(out_dtype, x.device, max(S, 0))
+    exactsum_sum_each(handle_for(dev), x.data_ptr() if x.numel() else None, off.data_ptr(), S, in_dtype,
+                      out_dtype, mode, out.data_ptr() if S > 0 else None, _stream_ptr(stream, dev))
     return out

@@ -62,7 +62,7 @@ __device__ __forceinline__ uint64_t encode(const OutFormat& f, uint32_t sign, ui
 
 // Round (-1)^sign * M * 2^unit_exp, M > 0 with bit length L, into format
 // `out` under `mode`.
-__device__ uint64_t round_magnitude(const uint32_t* m, int nl, int L, uint32_t sign, int unit_exp,
+static __device__ uint64_t round_magnitude(const uint32_t* m, int nl, int L, uint32_t sign, int unit_exp,
                                    int out, int mode) {
   const OutFormat f = out_format(out);
   const int P = f.frac_bits + 1;
@@ -100,7 +100,7 @@ __device__ uint64_t round_magnitude(const uint32_t* m, int nl, int L, uint32_t s
 // Result bits for an accumulator (ACC_WORDS words; digits need not be
 // regularised as long as |digit| < 2^62).  `limbs` is scratch for
 // ACC_DIGITS words.  One thread.
-__device__ uint64_t finalize_acc(const int64_t* acc, uint32_t* limbs, int in_dt, int out,
+static __device__ uint64_t finalize_acc(const int64_t* acc, uint32_t* limbs, int in_dt, int out,
                                  int mode) {
   const OutFormat f = out_format(out);
   const uint64_t sign_bit = (uint64_t)1 << (8 * f.width - 1);

@@ -1,0 +1,282 @@
+// segmented.cu -- many exact sums of CSR segments in one persistent launch.
+//
+// The MapReduce shape of Section 6.1, inside one GPU: the input is cut into
+// tiles (a segment of length L becomes ceil(L / TILE) tiles); every warp is
+// a reducer that pulls tiles from a work queue, sums its tile into private
+// superaccumulators and merges them carry-free (Lemma 1).  A tile that is a
+// whole segment is rounded by its warp at once.  Otherwise the warp adds its
+// 80-word partial into the segment's accumulator with integer atomics
+// (digit-wise addition is the carry-free superaccumulator sum, so the order
+// of arrival does not matter), and the warp that retires the segment's last
+// tile rounds it (the post-process of Section 6.1) and clears the
+// accumulator for the next call.  Nothing waits on anything: the last
+// arriver does the work.
+//
+// Launch sequence (captured once into a CUDA graph per call signature):
+//   seg_count_kernel   tiles per segment, summed per 1024-segment block
+//   seg_scan_kernel    exclusive scan of the block sums (one CTA)
+//   seg_base_kernel    per-segment first tile, tile->segment map, empty
+//                      segments answered (+0), invalid offsets flagged
+//   seg_sum_kernel     the persistent reducer kernel
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/exactsum.h"
+#include "digits.cuh"
+#include "finalize.cuh"
+#include "handle.h"
+#include "segmented.h"
+#include "stream.cuh"
+
+namespace es {
+
+constexpr int PLAN_T = 1024;
+
+__device__ __forceinline__ void store_indexed(void* results, int out, int64_t s, uint64_t bits) {
+  const int w = out == F64 ? 8 : (out == F32 ? 4 : 2);
+  store_result((char*)results + s * w, out, bits);
+}
+
+__device__ __forceinline__ uint64_t quiet_nan_bits(int out) {
+  return out == F64 ? 0x7FF8000000000000ull : (out == F32 ? 0x7FC00000ull : 0x7FC0ull);
+}
+
+__device__ __forceinline__ int64_t seg_tiles(const int64_t* off, int64_t s, int64_t tile, bool& bad) {
+  const int64_t a = off[s], b = off[s + 1];
+  if (a < 0 || b < a) {
+    bad = true;
+    return 0;
+  }
+  return (b - a + tile - 1) / tile;
+}
+
+// Block-wide exclusive scan of one int64 per thread (PLAN_T threads).
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* warp_tot, int64_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = (lane < PLAN_T / 32) ? warp_tot[lane] : 0;
+    int64_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < PLAN_T / 32) warp_tot[lane] = wi - w;  // exclusive warp offsets
+    if (lane == 31) warp_tot[32] = wi;
+  }
+  __syncthreads();
+  total = warp_tot[32];
+  const int64_t r = warp_tot[warp] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(PLAN_T) seg_count_kernel(SegArgs a) {
+  __shared__ int64_t warp_tot[33];
+  const int64_t s = (int64_t)blockIdx.x * PLAN_T + threadIdx.x;
+  bool bad = false;
+  const int64_t nt = (s < a.S) ? seg_tiles(a.off, s, a.tile, bad) : 0;
+  int64_t total;
+  block_exclusive_scan(nt, warp_tot, total);
+  if (threadIdx.x == 0) a.block_tiles[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(PLAN_T) seg_scan_kernel(SegArgs a, int64_t nblocks) {
+  __shared__ int64_t warp_tot[33];
+  int64_t running = 0;
+  for (int64_t base = 0; base < nblocks; base += PLAN_T) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = (i < nblocks) ? a.block_tiles[i] : 0;
+    int64_t total;
+    const int64_t ex = block_exclusive_scan(v, warp_tot, total);
+    if (i < nblocks) a.block_tiles[i] = running + ex;
+    running += total;
+  }
+  if (threadIdx.x == 0) {
+    a.counters[CNT_QUEUE] = 0;
+    a.counters[CNT_TOTAL] = (unsigned long long)running;
+    if ((int64_t)running > a.map_capacity) atomicOr(&a.counters[CNT_STATUS], STATUS_MAP_OVERFLOW);
+  }
+}
+
+__global__ void __launch_bounds__(PLAN_T) seg_base_kernel(SegArgs a) {
+  __shared__ int64_t warp_tot[33];
+  const int64_t s = (int64_t)blockIdx.x * PLAN_T + threadIdx.x;
+  bool bad = false;
+  const int64_t nt = (s < a.S) ? seg_tiles(a.off, s, a.tile, bad) : 0;
+  int64_t total;
+  const int64_t ex = block_exclusive_scan(nt, warp_tot, total);
+  const int64_t base = a.block_tiles[blockIdx.x] + ex;
+  const bool fits = (int64_t)__ldcg((const unsigned long long*)&a.counters[CNT_TOTAL]) <= a.map_capacity;
+  if (s < a.S) {
+    a.tile_base[s] = base;
+    a.remaining[s] = (unsigned)nt;
+    if (s == a.S - 1) a.tile_base[a.S] = base + nt;
+    if (nt == 0) store_indexed(a.results, a.out, s, bad ? quiet_nan_bits(a.out) : 0ull);
+    if (fits)
+      for (int64_t k = 0; k < nt; ++k) a.tile_seg[base + k] = (int32_t)s;
+    else if (nt > 0)
+      store_indexed(a.results, a.out, s, quiet_nan_bits(a.out));
+    if (bad) atomicOr(&a.counters[CNT_STATUS], STATUS_BAD_OFFSETS);
+  }
+}
+
+template <int DT, int W, int U>
+__global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel(SegArgs a) {
+  constexpr int T = W * 32;
+  constexpr int ND = Geometry<DT>::DIGITS;
+  constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
+  extern __shared__ int64_t digits[];  // ND x T
+  __shared__ int64_t wacc[W][ACC_WORDS];
+  __shared__ uint32_t wlimbs[W][ACC_DIGITS];
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  int64_t* col = digits + t;
+  for (int i = 0; i < ND; ++i) col[i * T] = 0;
+  const int64_t total = (int64_t)__ldcg((const unsigned long long*)&a.counters[CNT_TOTAL]);
+  if (total > a.map_capacity) return;  // flagged by the planner; results are NaN
+
+  for (;;) {
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(&a.counters[CNT_QUEUE], 1ull);
+    const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, tk, 0);
+    if (tile >= total) break;
+    const int64_t s = a.tile_seg[tile];
+    const int64_t tb = a.tile_base[s];
+    const int64_t ntiles = a.tile_base[s + 1] - tb;
+    const int64_t seg_lo = a.off[s], seg_hi = a.off[s + 1];
+    const int64_t lo = seg_lo + (tile - tb) * a.tile;
+    const int64_t hi = min(seg_hi, lo + a.tile);
+
+    // ---- accumulate this tile (warp-cooperative, lane-private columns) ----
+    const RangeSplit r = split_range<DT>(a.x, lo, hi);
+    uint32_t emax = 0;
+    int reg_left = REG_EVERY;
+    add_split<DT, T, 32, U>(col, a.x, r, lane, emax, reg_left);
+    regularise<DT, T>(col);
+    uint32_t flags = 24u;
+    if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) flags = rescan_split<DT, 32>(a.x, r, lane);
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    __syncwarp();
+
+    // ---- warp merge (carry-free), then clear the columns ----
+    int64_t d0, d1, d2;
+    warp_merge<DT, T>(digits + warp * 32, lane, d0, d1, d2);
+    __syncwarp();
+    for (int i = 0; i < ND; ++i) col[i * T] = 0;
+    if (lane + 64 >= ACC_DIGITS) d2 = (lane + 64 < ACC_WORDS) ? flag_word(lane + 64, flags, hi - lo) : 0;
+
+    if (ntiles == 1) {
+      wacc[warp][lane] = d0;
+      wacc[warp][lane + 32] = d1;
+      if (lane + 64 < ACC_WORDS) wacc[warp][lane + 64] = d2;
+      __syncwarp();
+      if (lane == 0) store_indexed(a.results, a.out, s, finalize_acc(wacc[warp], wlimbs[warp], DT, a.out, a.mode));
+      __syncwarp();
+    } else {
+      unsigned long long* acc = (unsigned long long*)(a.seg_acc + s * ACC_WORDS);
+      if (d0) atomicAdd(acc + lane, (unsigned long long)d0);
+      if (d1) atomicAdd(acc + lane + 32, (unsigned long long)d1);
+      if (lane + 64 < ACC_WORDS && d2) atomicAdd(acc + lane + 64, (unsigned long long)d2);
+      __threadfence();
+      __syncwarp();
+      unsigned last = 0;
+      if (lane == 0) last = (atomicSub(&a.remaining[s], 1u) == 1u) ? 1u : 0u;
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last) {
+        __threadfence();
+        wacc[warp][lane] = (int64_t)__ldcg(acc + lane);
+        wacc[warp][lane + 32] = (int64_t)__ldcg(acc + lane + 32);
+        if (lane + 64 < ACC_WORDS) wacc[warp][lane + 64] = (int64_t)__ldcg(acc + lane + 64);
+        acc[lane] = 0;
+        acc[lane + 32] = 0;
+        if (lane + 64 < ACC_WORDS) acc[lane + 64] = 0;
+        __syncwarp();
+        if (lane == 0) store_indexed(a.results, a.out, s, finalize_acc(wacc[warp], wlimbs[warp], DT, a.out, a.mode));
+        __syncwarp();
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <int DT, int W>
+static cudaError_t set_attr_t() {
+  constexpr int U = 4;
+  constexpr size_t SMEM = (size_t)Geometry<DT>::DIGITS * W * 32 * sizeof(int64_t);
+  return cudaFuncSetAttribute(seg_sum_kernel<DT, W, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SMEM);
+}
+
+template <int DT, int W>
+static void launch_main_direct(const SegArgs& a, int grid, cudaStream_t st) {
+  constexpr int U = 4;
+  constexpr size_t SMEM = (size_t)Geometry<DT>::DIGITS * W * 32 * sizeof(int64_t);
+  seg_sum_kernel<DT, W, U><<<grid, W * 32, SMEM, st>>>(a);
+}
+
+static cudaError_t configure_kernels(int dev) {
+  static bool done[64] = {};
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  cudaError_t e;
+  if ((e = set_attr_t<F64, 8>()) != cudaSuccess) return e;
+  if ((e = set_attr_t<F64, 12>()) != cudaSuccess) return e;
+  if ((e = set_attr_t<F32, 8>()) != cudaSuccess) return e;
+  if ((e = set_attr_t<F32, 16>()) != cudaSuccess) return e;
+  if ((e = set_attr_t<BF16, 8>()) != cudaSuccess) return e;
+  if ((e = set_attr_t<BF16, 16>()) != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return cudaSuccess;
+}
+
+int seg_warps_choice(int in_dt, int idx) {
+  if (in_dt == F64) return idx == 0 ? 8 : 12;
+  return idx == 0 ? 8 : 16;
+}
+
+cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int num_sms, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = configure_kernels(dev)) != cudaSuccess) return e;
+  const int64_t nblocks = (a.S + PLAN_T - 1) / PLAN_T;
+  seg_count_kernel<<<(unsigned)nblocks, PLAN_T, 0, st>>>(a);
+  seg_scan_kernel<<<1, PLAN_T, 0, st>>>(a, nblocks);
+  seg_base_kernel<<<(unsigned)nblocks, PLAN_T, 0, st>>>(a);
+  const int grid = num_sms;
+  switch (in_dt) {
+    case F64:
+      if (warps == 12) launch_main_direct<F64, 12>(a, grid, st);
+      else launch_main_direct<F64, 8>(a, grid, st);
+      break;
+    case F32:
+      if (warps == 16) launch_main_direct<F32, 16>(a, grid, st);
+      else launch_main_direct<F32, 8>(a, grid, st);
+      break;
+    default:
+      if (warps == 16) launch_main_direct<BF16, 16>(a, grid, st);
+      else launch_main_direct<BF16, 8>(a, grid, st);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace es

@@ -1,0 +1,33 @@
+// segmented.h -- arguments and launch entry of the segmented-sum kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace es {
+
+enum : int { CNT_QUEUE = 0, CNT_TOTAL = 1, CNT_STATUS = 2 };
+enum : unsigned long long { STATUS_BAD_OFFSETS = 1ull, STATUS_MAP_OVERFLOW = 2ull };
+
+struct SegArgs {
+  const void* x;                 // elements (element-aligned)
+  const int64_t* off;            // S + 1 CSR offsets (device)
+  int64_t S;
+  int out, mode;
+  void* results;                 // S elements of the output format
+  int64_t tile;                  // elements per tile
+  int64_t* block_tiles;          // ceil(S / 1024) per-block tile sums, then their scan
+  int64_t* tile_base;            // S + 1: first tile of each segment
+  int32_t* tile_seg;             // map_capacity: segment of each tile
+  int64_t map_capacity;
+  unsigned int* remaining;       // S: tiles not yet retired
+  int64_t* seg_acc;              // S x ACC_WORDS, zero between calls
+  unsigned long long* counters;  // CNT_* words
+};
+
+// Enqueue the four kernels of one segmented sum on `st`.
+cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int num_sms, cudaStream_t st);
+// Warps per CTA of the reducer kernel for a dtype: choice 0 or 1.
+int seg_warps_choice(int in_dt, int idx);
+
+}  // namespace es

@@ -22,22 +22,9 @@
 #include "digits.cuh"
 #include "finalize.cuh"
 #include "internal.h"
+#include "stream.cuh"
 
 namespace es {
-
-__device__ __forceinline__ uint4 ldg_stream(const uint4* p) {
-  uint4 r;
-  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
-      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-      : "l"(p));
-  return r;
-}
-
-__device__ __forceinline__ int64_t warp_sum(int64_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // Elements owned by thread t of CTA b: vectors vb + t + j*T (< ve), the
 // unaligned head (CTA 0) and the ragged tail (last CTA).
@@ -58,10 +45,8 @@ __device__ uint32_t rescan_flags(const SumArgs& a, int64_t vb, int64_t ve) {
 template <int DT, int T, int U>
 __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   constexpr int ND = Geometry<DT>::DIGITS;
-  constexpr int EPV = 16 / Geometry<DT>::ELEM_BYTES;
   constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
   constexpr int NW = T / 32;
-  constexpr int64_t PER = (int64_t)T * U;
   static_assert(ND * T >= NW * ACC_WORDS, "digit area reused for the grid merge");
 
   extern __shared__ int64_t digits[];  // ND x T
@@ -79,43 +64,13 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   const uint4* vx = reinterpret_cast<const uint4*>((const char*)a.x + a.head * Geometry<DT>::ELEM_BYTES);
   const int64_t G = gridDim.x;
   const int64_t vb = a.nvec * blockIdx.x / G, ve = a.nvec * (blockIdx.x + 1) / G;
-  const int64_t nb = (ve - vb) / PER;
-  const uint4* p = vx + vb + t;
   int reg_left = REG_EVERY;
 
-  // ---- hot loop: full batches of U vectors per thread, double buffered ----
-  uint4 A[U], B[U];
-  if (nb > 0) {
-#pragma unroll
-    for (int u = 0; u < U; ++u) A[u] = ldg_stream(p + u * T);
-  }
-  for (int64_t k = 0; k < nb; k += 2) {
-    if (k + 1 < nb) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) B[u] = ldg_stream(p + (k + 1) * PER + u * T);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) add_vec<DT, T>(col, A[u], emax);
-    reg_left -= U * EPV;
-    if (reg_left <= 0) {
-      regularise<DT, T>(col);
-      reg_left = REG_EVERY;
-    }
-    if (k + 1 >= nb) break;
-    if (k + 2 < nb) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) A[u] = ldg_stream(p + (k + 2) * PER + u * T);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) add_vec<DT, T>(col, B[u], emax);
-    reg_left -= U * EPV;
-    if (reg_left <= 0) {
-      regularise<DT, T>(col);
-      reg_left = REG_EVERY;
-    }
-  }
-  // ---- ragged remainder of this CTA's vectors, head and tail ----
-  for (int64_t v = vb + nb * PER + t; v < ve; v += T) add_vec<DT, T>(col, ldg_stream(vx + v), emax);
+  // ---- hot loop: this thread's vectors vb + t + j*T, double buffered ----
+  const int64_t cnt = (vb + t < ve) ? (ve - vb - t + T - 1) / T : 0;
+  stream_add<DT, T, T, U>(col, vx + vb + t, cnt, emax, reg_left, t, vx + ve);
+
+  // ---- unaligned head (CTA 0) and ragged tail (last CTA) ----
   if (blockIdx.x == 0 && t < a.head) add_one<DT, T>(col, load_one<DT>(a.x, t), emax);
   if (blockIdx.x == G - 1 && t < a.tail) add_one<DT, T>(col, load_one<DT>(a.x, a.n - a.tail + t), emax);
   regularise<DT, T>(col);
@@ -199,9 +154,27 @@ __global__ void round_acc_kernel(const int64_t* acc, int in_dt, int out, int mod
 // ---------------------------------------------------------------------------
 template <int DT>
 struct SumConfig;
-template <> struct SumConfig<F64> { static constexpr int T = 384, U = 4; };
-template <> struct SumConfig<F32> { static constexpr int T = 512, U = 4; };
-template <> struct SumConfig<BF16> { static constexpr int T = 512, U = 2; };
+#ifndef ES_F64_T
+#define ES_F64_T 384
+#endif
+#ifndef ES_F64_U
+#define ES_F64_U 4
+#endif
+#ifndef ES_F32_T
+#define ES_F32_T 512
+#endif
+#ifndef ES_F32_U
+#define ES_F32_U 4
+#endif
+#ifndef ES_BF16_T
+#define ES_BF16_T 512
+#endif
+#ifndef ES_BF16_U
+#define ES_BF16_U 2
+#endif
+template <> struct SumConfig<F64> { static constexpr int T = ES_F64_T, U = ES_F64_U; };
+template <> struct SumConfig<F32> { static constexpr int T = ES_F32_T, U = ES_F32_U; };
+template <> struct SumConfig<BF16> { static constexpr int T = ES_BF16_T, U = ES_BF16_U; };
 
 template <int DT>
 static cudaError_t launch_sum_t(const SumArgs& a0, int max_ctas, cudaStream_t stream, int* grid_out) {

@@ -41,6 +41,7 @@ void es_workspace_free(exactsum_t h) {
   cudaFree(h->host_acc);
   cudaFree(h->d_result_tmp);
   if (h->h_result_pinned) cudaFreeHost(h->h_result_pinned);
+  es_segment_free_extra(h);
   cudaFree(h->seg_acc);
   cudaFree(h->seg_tile_base);
   cudaFree(h->seg_remaining);

@@ -143,7 +143,8 @@ def segmented_f64(lengths: np.ndarray, seed: int = 0, kmin: int = -200,
     ks = rng.integers(kmin, kmax + 1, len(lengths))
     for L, k in zip(lengths.tolist(), ks.tolist()):
         v = rng.standard_normal(L) * math.ldexp(1.0, k)
-        v -= v.mean()
+        if L:
+            v -= v.mean()
         out[pos:pos + L] = v
         pos += L
     return out.view(np.uint64)

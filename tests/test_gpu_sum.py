@@ -107,7 +107,7 @@ def test_signed_zero_rules():
             elif pattern == "poszero":
                 bits = np.zeros(n, dtype=np.uint64)
             elif pattern == "mixed":
-                bits = np.where(np.arange(n) % 3 == 0, 1 << 63, 0).astype(np.uint64)
+                bits = np.where(np.arange(n) % 3 == 0, np.uint64(1 << 63), np.uint64(0)).astype(np.uint64)
             elif pattern == "cancel":
                 v = W.uniform_f64(n // 2 + 1, n)
                 bits = np.concatenate([v, v ^ np.uint64(1 << 63)])
