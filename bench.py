@@ -133,6 +133,107 @@ def cpu_baseline(bits, passes: int):
                       f"({dt:.2f} s wall)"}
 
 
+def bench_segmented(es, W, torch, dev, steps):
+    """65,536 FP64 segments with log-uniform lengths in [1, 2^20] (Anderson-style
+    mean-subtracted Gaussians scaled by 2^k, k uniform in [-200, 200]): the
+    batched call (one graph-captured launch sequence, autotuned) against one
+    exactsum_sum launch per segment, same results bit for bit."""
+    lengths = W.segment_lengths(65536, seed=0)
+    off = W.csr_offsets(lengths)
+    total = int(off[-1])
+    x = W.segmented_f64_device(lengths, seed=0, device=dev)
+    d_off = torch.from_numpy(off).to(dev)
+    h_off = torch.from_numpy(off)
+    h = es.handle_for(dev.index)
+    stream = torch.cuda.current_stream(dev)
+    out_b = torch.empty(len(lengths), dtype=torch.float64, device=dev)
+    out_e = torch.empty(len(lengths), dtype=torch.float64, device=dev)
+    warps, tile, tune_ms = es.exactsum_segmented_autotune(h, x.data_ptr(), d_off.data_ptr(), len(lengths),
+                                                          es.F64, out_b.data_ptr(), stream.cuda_stream)
+
+    def timed(fn, k):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / k
+
+    batched_ms = timed(lambda: es.segmented_sum(x, d_off, out=out_b), max(3, steps))
+    each_ms = timed(lambda: es.sum_each(x, h_off, out=out_e), 2)
+    same = bool(torch.equal(out_b.view(torch.int64), out_e.view(torch.int64)))
+    r = {"workload": "65,536 FP64 segments, lengths log-uniform [1, 2^20] (seed 0), N(0,1)*2^k, "
+                     "k in [-200,200], minus the segment mean (device-generated)",
+         "segments": len(lengths), "elements": total, "bytes": total * 8,
+         "batched_ms": round(batched_ms, 3), "per_segment_ms": round(each_ms, 3),
+         "speedup_vs_per_segment": round(each_ms / batched_ms, 2),
+         "batched_gelem_s": round(total / batched_ms / 1e6, 2),
+         "batched_hbm_gbs": round(total * 8 / batched_ms / 1e6, 1),
+         "tuned": {"warps": warps, "tile": tile, "ms": round(tune_ms, 3)},
+         "bit_identical_to_per_segment": same}
+    del x
+    torch.cuda.empty_cache()
+    return r
+
+
+def bench_serving(es, W, torch, dev, num_requests=100_000):
+    """Poisson stream of requests at 20k req/s (mean gap 50 us), sizes
+    floor(2^(10 + 16U)), FP64 with p = 0.8 else FP32, windows into 2^26-element
+    uniform [-1,1) device pools; served by the continuous-batching engine."""
+    req = W.serving_requests(num_requests, seed=0)
+    pools = W.serving_pools(26, seed=0)
+    d = {es.F64: torch.from_numpy(pools[es.F64].view(np.int64)).to(dev),
+         es.F32: torch.from_numpy(pools[es.F32].view(np.int32)).to(dev)}
+    base = {k: v.data_ptr() for k, v in d.items()}
+    isz = {es.F64: 8, es.F32: 4}
+    budget = 4 << 30
+    server = es.exactsum_server_create(dev.index, 128, budget, 1 << 21, 1 << 15)
+    try:
+        ns, dts, offs, arr = (req["n"].tolist(), req["dtype"].tolist(), req["offset"].tolist(),
+                              req["arrival_us"].tolist())
+        # warm the engine with a few requests
+        for k in range(8):
+            es.exactsum_server_submit(server, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k], dts[k], es.RNE, 0)
+        es.exactsum_server_drain(server, 60_000)
+        es.exactsum_server_poll(server)
+        t0 = time.perf_counter()
+        for k in range(len(ns)):
+            target = arr[k] * 1e-6
+            while time.perf_counter() - t0 < target:
+                pass
+            es.exactsum_server_submit(server, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k], dts[k],
+                                      es.RNE, 0)
+        submit_span = time.perf_counter() - t0
+        es.exactsum_server_drain(server, 600_000)
+        recs = []
+        while True:
+            got = es.exactsum_server_poll(server, 65536)
+            if not got:
+                break
+            recs.extend(got)
+        stats = es.exactsum_server_stats(server)
+    finally:
+        es.exactsum_server_destroy(server)
+    lat = np.array([r.done_ns - r.submit_ns for r in recs], dtype=np.float64) / 1e3
+    ok = sum(1 for r in recs if r.status == es.OK)
+    first = min(r.submit_ns for r in recs)
+    last = max(r.done_ns for r in recs)
+    elems = float(sum(ns))
+    return {"workload": "100,000 requests, Poisson 20k req/s, n = floor(2^(10+16U)), 80% FP64 / 20% FP32, "
+                        "windows of 2^26-element uniform [-1,1) device pools (seed 0)",
+            "requests": len(recs), "ok": ok, "offered_req_s": round(len(ns) / submit_span, 1),
+            "p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),
+            "mean_us": round(float(lat.mean()), 1), "max_us": round(float(lat.max()), 1),
+            "gelem_s": round(elems / ((last - first) * 1e-9) / 1e9, 2),
+            "engine": {"max_slots": 128, "budget_bytes": budget, "chunk_elems": 1 << 21, "tile_elems": 1 << 15,
+                       "steps": stats["steps"], "peak_resident": stats["peak_active"]}}
+
+
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -267,7 +368,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_kind": f"{peak_kind} (STREAM-style copy)",
-                     "kernel": "es::sum_kernel<F64,384,4>",
+                     "kernel": "es::sum_kernel_tma<F64, 8 consumer warps, 8 vectors/stage, 2 stages>",
                      "algorithmic_bytes_per_launch": n * BYTES_PER_ELEM,
                      "avg_kernel_ms": round(avg_kernel_ms, 4)},
         "e2e": e2e,
@@ -279,6 +380,11 @@ def run_ours(args):
         line["config"]["workload"] = f"profiling case: n = 2^{args.log2n}, same recipe"
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(bits, passes=3)
+    if ws == 1 and args.log2n == LOG2N and not args.primary_only:
+        del x
+        torch.cuda.empty_cache()
+        line["segmented"] = bench_segmented(es, W, torch, dev, args.steps)
+        line["serving"] = bench_serving(es, W, torch, dev)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -294,6 +400,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--primary-only", action="store_true",
+                    help="skip the segmented and serving measurements")
     ap.add_argument("--log2n", type=int, default=LOG2N,
                     help="smaller cases for profiling only; the benchmark line uses 2^28")
     args = ap.parse_args()

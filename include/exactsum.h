@@ -172,6 +172,7 @@ exactsum_status exactsum_acc_round(exactsum_t h, const void* d_acc, int in_dtype
 /* Device status bits reported by exactsum_device_status. */
 #define EXACTSUM_STATUS_BAD_OFFSETS 1  /* a segment had offsets[s+1] < offsets[s] or offsets[s] < 0 */
 #define EXACTSUM_STATUS_MAP_OVERFLOW 2 /* more tiles than the tile map holds (input larger than HBM) */
+#define EXACTSUM_STATUS_TIMEOUT 4      /* a bounded wait inside a kernel gave up; that result is invalid */
 
 /* d_results[s] <- round(sum of d_x[d_offsets[s] .. d_offsets[s+1])) for
  * s in [0, num_segments).
@@ -217,6 +218,75 @@ exactsum_status exactsum_tuning_load(exactsum_t h, const char* path);
 /* Synchronise the handle's device, return the accumulated device status
  * bits (EXACTSUM_STATUS_*) in *status_out and clear them. */
 exactsum_status exactsum_device_status(exactsum_t h, int64_t* status_out);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of exact-sum requests                      */
+/* (no paper counterpart: the reducer state of Section 6.1 kept on the     */
+/* device while requests of mixed sizes come and go)                       */
+/* ---------------------------------------------------------------------- */
+
+typedef struct exactsum_server* exactsum_server_t;
+
+/* One finished request, as reported by exactsum_server_poll. */
+typedef struct {
+    uint64_t id;           /* from exactsum_server_submit */
+    int32_t status;        /* EXACTSUM_OK; EXACTSUM_ENOMEM if staging memory could not be
+                              allocated; EXACTSUM_ECUDA if the engine failed */
+    int32_t out_dtype;
+    uint64_t result_bits;  /* the rounded sum in the low 16/32/64 bits */
+    int64_t n;
+    int64_t submit_ns;     /* exactsum_server_clock_ns() at submission, */
+    int64_t admit_ns;      /* at admission into a slot, */
+    int64_t done_ns;       /* when the result was visible on the host */
+} exactsum_completion;
+
+/* Start a serving engine on `device` with its own streams and a scheduler
+ * thread.
+ *   max_slots (1..256): requests resident at once; each owns one device
+ *     accumulator slot for its whole life, across steps.
+ *   mem_budget_bytes: admission limit on the bytes held by resident
+ *     requests (input bytes + EXACTSUM_ACC_BYTES each).  A request waits,
+ *     in arrival order, until a slot is free and the budget has room; a
+ *     request larger than the whole budget is admitted alone.
+ *   chunk_elems: elements of each request processed per step (continuous
+ *     batching: every step carries one chunk of every resident request, in
+ *     one kernel, so requests that arrive later join at the next step).
+ *   tile_elems: elements per warp work unit (multiple of 64 dividing
+ *     chunk_elems). */
+exactsum_status exactsum_server_create(exactsum_server_t* out, int device, int max_slots,
+                                       int64_t mem_budget_bytes, int64_t chunk_elems,
+                                       int64_t tile_elems);
+
+/* Queue a request: the exact sum of x[0..n) (in_dtype) rounded to
+ * out_dtype under mode.  x_on_host = 0: x is device memory that must stay
+ * valid and unchanged until the request completes.  x_on_host = 1: x is
+ * host memory (page-locked for speed); the engine copies it to the device
+ * after admission, and x must stay valid until completion.  Thread-safe;
+ * returns at once with the request id in *id_out. */
+exactsum_status exactsum_server_submit(exactsum_server_t s, const void* x, int64_t n, int in_dtype,
+                                       int out_dtype, int mode, int x_on_host, uint64_t* id_out);
+
+/* Move up to max_out completion records into out; *count receives how many. */
+exactsum_status exactsum_server_poll(exactsum_server_t s, exactsum_completion* out, int max_out,
+                                     int* count);
+
+/* Wait until every submitted request has completed (EXACTSUM_ETIMEOUT after
+ * timeout_ms milliseconds). */
+exactsum_status exactsum_server_drain(exactsum_server_t s, int64_t timeout_ms);
+
+/* Counters: steps launched, most requests resident at once, requests not yet complete. */
+exactsum_status exactsum_server_stats(exactsum_server_t s, int64_t* steps, int64_t* peak_active,
+                                      int64_t* outstanding);
+
+/* The engine's steady clock, in nanoseconds. */
+int64_t exactsum_server_clock_ns(void);
+
+/* Message for the server's last failure. */
+const char* exactsum_server_last_error(exactsum_server_t s);
+
+/* Finish every request still in the system, stop the scheduler and free
+ * the engine. */
+exactsum_status exactsum_server_destroy(exactsum_server_t s);
 
 #ifdef __cplusplus
 }

@@ -52,6 +52,12 @@ _SIGNATURES = {
     "exactsum_tuning_save": [_vp, ctypes.c_char_p],
     "exactsum_tuning_load": [_vp, ctypes.c_char_p],
     "exactsum_device_status": [_vp, ctypes.POINTER(_i64)],
+    "exactsum_server_create": [ctypes.POINTER(_vp), _int, _int, _i64, _i64, _i64],
+    "exactsum_server_submit": [_vp, _vp, _i64, _int, _int, _int, _int, ctypes.POINTER(ctypes.c_uint64)],
+    "exactsum_server_poll": [_vp, _vp, _int, ctypes.POINTER(_int)],
+    "exactsum_server_drain": [_vp, _i64],
+    "exactsum_server_stats": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
+    "exactsum_server_destroy": [_vp],
 }
 OPTIONAL_SIGNATURES: dict = {}
 
@@ -96,6 +102,10 @@ def library() -> ctypes.CDLL:
                 fn.restype = _int
             lib.exactsum_last_error.argtypes = [_vp]
             lib.exactsum_last_error.restype = ctypes.c_char_p
+            lib.exactsum_server_last_error.argtypes = [_vp]
+            lib.exactsum_server_last_error.restype = ctypes.c_char_p
+            lib.exactsum_server_clock_ns.argtypes = []
+            lib.exactsum_server_clock_ns.restype = _i64
             _lib = lib
     return _lib
 
@@ -183,6 +193,63 @@ def exactsum_device_status(handle) -> int:
 
 
 STATUS_BAD_OFFSETS, STATUS_MAP_OVERFLOW = 1, 2
+
+
+class exactsum_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
+                ("result_bits", ctypes.c_uint64), ("n", ctypes.c_int64), ("submit_ns", ctypes.c_int64),
+                ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+def _check_server(status: int, server) -> None:
+    if status != OK:
+        msg = library().exactsum_server_last_error(server) if server else b"invalid argument"
+        raise ExactSumError(status, msg.decode(errors="replace") if msg else "")
+
+
+def exactsum_server_create(device: int, max_slots: int, mem_budget_bytes: int, chunk_elems: int,
+                           tile_elems: int) -> int:
+    h = _vp()
+    _check_server(library().exactsum_server_create(ctypes.byref(h), device, max_slots, mem_budget_bytes,
+                                                   chunk_elems, tile_elems), None)
+    return h.value
+
+
+def exactsum_server_submit(server, x, n, in_dtype, out_dtype, mode, x_on_host) -> int:
+    rid = ctypes.c_uint64(0)
+    _check_server(library().exactsum_server_submit(server, x, n, in_dtype, out_dtype, mode, x_on_host,
+                                                   ctypes.byref(rid)), server)
+    return rid.value
+
+
+def exactsum_server_poll(server, max_out: int = 4096) -> list:
+    buf = (exactsum_completion * max_out)()
+    cnt = _int(0)
+    _check_server(library().exactsum_server_poll(server, buf, max_out, ctypes.byref(cnt)), server)
+    return [buf[i] for i in range(cnt.value)]
+
+
+def exactsum_server_drain(server, timeout_ms: int) -> None:
+    _check_server(library().exactsum_server_drain(server, timeout_ms), server)
+
+
+def exactsum_server_stats(server):
+    a, b, c = _i64(0), _i64(0), _i64(0)
+    _check_server(library().exactsum_server_stats(server, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+                  server)
+    return {"steps": a.value, "peak_active": b.value, "outstanding": c.value}
+
+
+def exactsum_server_clock_ns() -> int:
+    return library().exactsum_server_clock_ns()
+
+
+def exactsum_server_last_error(server) -> str:
+    return library().exactsum_server_last_error(server).decode(errors="replace")
+
+
+def exactsum_server_destroy(server) -> None:
+    _check_server(library().exactsum_server_destroy(server), server)
 
 
 # ---------------------------------------------------------------------------

@@ -114,6 +114,7 @@ exactsum_status exactsum_sum(exactsum_t h, const void* d_x, int64_t n, int in_dt
   a.acc = nullptr;
   a.partials = h->partials;
   a.ticket = h->ticket;
+  a.status = h->dev_status;
   cudaError_t e = es::launch_sum(in_dtype, a, h->max_ctas, (cudaStream_t)stream, nullptr);
   if (e != cudaSuccess) return es_cuda_fail(h, e, "sum kernel launch");
   return EXACTSUM_OK;
@@ -143,6 +144,7 @@ exactsum_status exactsum_acc_add(exactsum_t h, const void* d_x, int64_t n, int i
   a.acc = (int64_t*)d_acc;
   a.partials = h->partials;
   a.ticket = h->ticket;
+  a.status = h->dev_status;
   cudaError_t e = es::launch_sum(in_dtype, a, h->max_ctas, (cudaStream_t)stream, nullptr);
   if (e != cudaSuccess) return es_cuda_fail(h, e, "accumulate kernel launch");
   return EXACTSUM_OK;

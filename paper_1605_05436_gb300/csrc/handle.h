@@ -43,6 +43,7 @@ struct exactsum_ctx {
   int64_t* partials = nullptr;      // partial_rows x ACC_WORDS
   int partial_rows = 0;
   unsigned int* ticket = nullptr;
+  unsigned long long* dev_status = nullptr;  // STATUS_* bits set by kernels
 
   // host-buffer pipeline (exactsum_sum_host)
   cudaStream_t copy_stream = nullptr;

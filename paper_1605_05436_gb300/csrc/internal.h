@@ -18,11 +18,14 @@ struct SumArgs {
   int64_t* acc;        // accumulator to add into (accumulate mode), or null
   int64_t* partials;   // grid x ACC_WORDS scratch
   unsigned int* ticket;  // zero between launches; reset by the last CTA
+  unsigned long long* status;  // device status word (STATUS_* bits)
 };
+
+// Device status bits (also in include/exactsum.h as EXACTSUM_STATUS_*).
+constexpr unsigned long long STATUS_BAD_OFFSETS = 1ull, STATUS_MAP_OVERFLOW = 2ull, STATUS_TIMEOUT = 4ull;
 
 cudaError_t launch_sum(int in_dt, const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out);
 cudaError_t launch_round_acc(const int64_t* acc, int in_dt, int out, int mode, void* result,
                              cudaStream_t stream);
-int sum_threads_per_cta(int in_dt);
 
 }  // namespace es

@@ -106,6 +106,7 @@ es::SegArgs make_args(exactsum_t h, const void* x, const int64_t* off, int64_t S
   a.remaining = h->seg_remaining;
   a.seg_acc = h->seg_acc;
   a.counters = h->seg_counters;
+  a.status = h->dev_status;
   return a;
 }
 
@@ -313,13 +314,12 @@ exactsum_status exactsum_device_status(exactsum_t h, int64_t* status_out) {
   *status_out = 0;
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return es_cuda_fail(h, e, "cudaSetDevice");
-  if (!h->seg_counters) return EXACTSUM_OK;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return es_cuda_fail(h, e, "cudaDeviceSynchronize");
   unsigned long long v = 0;
-  if ((e = cudaMemcpy(&v, h->seg_counters + es::CNT_STATUS, sizeof v, cudaMemcpyDeviceToHost)) != cudaSuccess)
+  if ((e = cudaMemcpy(&v, h->dev_status, sizeof v, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return es_cuda_fail(h, e, "cudaMemcpy(status)");
   const unsigned long long zero = 0;
-  if ((e = cudaMemcpy(h->seg_counters + es::CNT_STATUS, &zero, sizeof zero, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = cudaMemcpy(h->dev_status, &zero, sizeof zero, cudaMemcpyHostToDevice)) != cudaSuccess)
     return es_cuda_fail(h, e, "cudaMemcpy(status)");
   *status_out = (int64_t)v;
   return EXACTSUM_OK;

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(PLAN_T) seg_scan_kernel(SegArgs a, int64_t nbl
   if (threadIdx.x == 0) {
     a.counters[CNT_QUEUE] = 0;
     a.counters[CNT_TOTAL] = (unsigned long long)running;
-    if ((int64_t)running > a.map_capacity) atomicOr(&a.counters[CNT_STATUS], STATUS_MAP_OVERFLOW);
+    if ((int64_t)running > a.map_capacity) atomicOr(a.status, STATUS_MAP_OVERFLOW);
   }
 }
 
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(PLAN_T) seg_base_kernel(SegArgs a) {
       for (int64_t k = 0; k < nt; ++k) a.tile_seg[base + k] = (int32_t)s;
     else if (nt > 0)
       store_indexed(a.results, a.out, s, quiet_nan_bits(a.out));
-    if (bad) atomicOr(&a.counters[CNT_STATUS], STATUS_BAD_OFFSETS);
+    if (bad) atomicOr(a.status, STATUS_BAD_OFFSETS);
   }
 }
 

@@ -4,10 +4,11 @@
 
 #include <cstdint>
 
+#include "internal.h"
+
 namespace es {
 
-enum : int { CNT_QUEUE = 0, CNT_TOTAL = 1, CNT_STATUS = 2 };
-enum : unsigned long long { STATUS_BAD_OFFSETS = 1ull, STATUS_MAP_OVERFLOW = 2ull };
+enum : int { CNT_QUEUE = 0, CNT_TOTAL = 1 };
 
 struct SegArgs {
   const void* x;                 // elements (element-aligned)
@@ -23,6 +24,7 @@ struct SegArgs {
   unsigned int* remaining;       // S: tiles not yet retired
   int64_t* seg_acc;              // S x ACC_WORDS, zero between calls
   unsigned long long* counters;  // CNT_* words
+  unsigned long long* status;    // device status word (STATUS_* bits)
 };
 
 // Enqueue the four kernels of one segmented sum on `st`.

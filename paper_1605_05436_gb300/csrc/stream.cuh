@@ -25,7 +25,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
 }
 
 #ifndef ES_PREFETCH_BATCHES
-#define ES_PREFETCH_BATCHES 4
+#define ES_PREFETCH_BATCHES 0
 #endif
 
 __device__ __forceinline__ int64_t warp_sum(int64_t v) {

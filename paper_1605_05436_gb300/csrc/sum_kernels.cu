@@ -23,6 +23,7 @@
 #include "finalize.cuh"
 #include "internal.h"
 #include "stream.cuh"
+#include "tma.cuh"
 
 namespace es {
 
@@ -42,71 +43,31 @@ __device__ uint32_t rescan_flags(const SumArgs& a, int64_t vb, int64_t ve) {
   return f;
 }
 
-template <int DT, int T, int U>
-__global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
-  constexpr int ND = Geometry<DT>::DIGITS;
-  constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
-  constexpr int NW = T / 32;
-  static_assert(ND * T >= NW * ACC_WORDS, "digit area reused for the grid merge");
-
-  extern __shared__ int64_t digits[];  // ND x T
-  __shared__ int64_t blk[ACC_WORDS];
-  __shared__ uint32_t limbs[ACC_DIGITS];
-  __shared__ uint32_t blk_flags, is_last;
-
+// CTA merge and grid merge, shared by both single-array kernels.  Called by
+// every thread of the CTA after its flags are in blk_flags and a barrier.
+// TC threads own digit columns (digit-major, stride TC); NW warps take part.
+template <int DT, int TC, int NW>
+__device__ __forceinline__ void finish_cta(const SumArgs& a, int64_t* digits, int64_t* blk, uint32_t* limbs,
+                                           uint32_t blk_flags, uint32_t* is_last) {
+  static_assert(Geometry<DT>::DIGITS * TC >= NW * ACC_WORDS, "digit area reused for the grid merge");
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  int64_t* col = digits + t;
-#pragma unroll 4
-  for (int i = 0; i < ND; ++i) col[i * T] = 0;
-  if (t == 0) blk_flags = 0;
-
-  uint32_t emax = 0;
-  const uint4* vx = reinterpret_cast<const uint4*>((const char*)a.x + a.head * Geometry<DT>::ELEM_BYTES);
   const int64_t G = gridDim.x;
-  const int64_t vb = a.nvec * blockIdx.x / G, ve = a.nvec * (blockIdx.x + 1) / G;
-  int reg_left = REG_EVERY;
-
-  // ---- hot loop: this thread's vectors vb + t + j*T, double buffered ----
-  const int64_t cnt = (vb + t < ve) ? (ve - vb - t + T - 1) / T : 0;
-  stream_add<DT, T, T, U>(col, vx + vb + t, cnt, emax, reg_left, t, vx + ve);
-
-  // ---- unaligned head (CTA 0) and ragged tail (last CTA) ----
-  if (blockIdx.x == 0 && t < a.head) add_one<DT, T>(col, load_one<DT>(a.x, t), emax);
-  if (blockIdx.x == G - 1 && t < a.tail) add_one<DT, T>(col, load_one<DT>(a.x, a.n - a.tail + t), emax);
-  regularise<DT, T>(col);
-
-  // ---- special values and signed zeros: exact rescan only when needed ----
-  uint32_t flags = 24u;  // an element with 0 < E < all-ones is neither +0 nor -0
-  if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) flags = rescan_flags<DT, T>(a, vb, ve);
-  __syncthreads();
-  if (flags) atomicOr(&blk_flags, flags);
-
-  // ---- CTA merge: sum the threads' digits, carry-free ----
+  // ---- CTA merge: sum the columns' digits, carry-free ----
   for (int i = warp; i < ACC_DIGITS; i += NW) {
     int64_t s = 0;
-    for (int j = lane; j < T; j += 32) s += digit32<DT, T>(digits + j, i);
+    for (int j = lane; j < TC; j += 32) s += digit32<DT, TC>(digits + j, i);
     s = warp_sum(s);
     if (lane == 0) blk[i] = s;
   }
-  __syncthreads();
-  if (t < ACC_WORDS - ACC_DIGITS) {
-    const int w = ACC_DIGITS + t;
-    int64_t v = 0;
-    if (w == W_NAN) v = (blk_flags & 1u) ? 1 : 0;
-    else if (w == W_PINF) v = (blk_flags & 2u) ? 1 : 0;
-    else if (w == W_NINF) v = (blk_flags & 4u) ? 1 : 0;
-    else if (w == W_NOTPZ) v = (blk_flags & 8u) ? 1 : 0;
-    else if (w == W_NOTNZ) v = (blk_flags & 16u) ? 1 : 0;
-    else if (w == W_COUNT) v = (blockIdx.x == 0) ? a.n : 0;
-    blk[w] = v;
-  }
+  if (t < ACC_WORDS - ACC_DIGITS)
+    blk[ACC_DIGITS + t] = flag_word(ACC_DIGITS + t, blk_flags, blockIdx.x == 0 ? a.n : 0);
   __syncthreads();
   if (t < ACC_WORDS) a.partials[blockIdx.x * ACC_WORDS + t] = blk[t];
   __threadfence();
   __syncthreads();
-  if (t == 0) is_last = (atomicAdd(a.ticket, 1u) == (unsigned)(G - 1)) ? 1u : 0u;
+  if (t == 0) *is_last = (atomicAdd(a.ticket, 1u) == (unsigned)(G - 1)) ? 1u : 0u;
   __syncthreads();
-  if (!is_last) return;
+  if (!*is_last) return;
 
   // ---- last CTA: merge the partial accumulators (post-process) ----
   __threadfence();
@@ -139,6 +100,167 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   }
 }
 
+// Register-streaming form: every thread loads its own vectors (16-byte
+// read-only loads, double buffered) and owns one digit column.
+template <int DT, int T, int U>
+__global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
+  constexpr int ND = Geometry<DT>::DIGITS;
+  constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
+  constexpr int NW = T / 32;
+
+  extern __shared__ int64_t digits[];  // ND x T
+  __shared__ int64_t blk[ACC_WORDS];
+  __shared__ uint32_t limbs[ACC_DIGITS];
+  __shared__ uint32_t blk_flags, is_last;
+
+  const int t = threadIdx.x;
+  int64_t* col = digits + t;
+#pragma unroll 4
+  for (int i = 0; i < ND; ++i) col[i * T] = 0;
+  if (t == 0) blk_flags = 0;
+
+  uint32_t emax = 0;
+  const uint4* vx = reinterpret_cast<const uint4*>((const char*)a.x + a.head * Geometry<DT>::ELEM_BYTES);
+  const int64_t G = gridDim.x;
+  const int64_t vb = a.nvec * blockIdx.x / G, ve = a.nvec * (blockIdx.x + 1) / G;
+  int reg_left = REG_EVERY;
+
+  // ---- hot loop: this thread's vectors vb + t + j*T, double buffered ----
+  const int64_t cnt = (vb + t < ve) ? (ve - vb - t + T - 1) / T : 0;
+  stream_add<DT, T, T, U>(col, vx + vb + t, cnt, emax, reg_left, t, vx + ve);
+
+  // ---- unaligned head (CTA 0) and ragged tail (last CTA) ----
+  if (blockIdx.x == 0 && t < a.head) add_one<DT, T>(col, load_one<DT>(a.x, t), emax);
+  if (blockIdx.x == G - 1 && t < a.tail) add_one<DT, T>(col, load_one<DT>(a.x, a.n - a.tail + t), emax);
+  regularise<DT, T>(col);
+
+  // ---- special values and signed zeros: exact rescan only when needed ----
+  uint32_t flags = 24u;  // an element with 0 < E < all-ones is neither +0 nor -0
+  if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) flags = rescan_flags<DT, T>(a, vb, ve);
+  __syncthreads();
+  if (flags) atomicOr(&blk_flags, flags);
+  __syncthreads();
+  finish_cta<DT, T, NW>(a, digits, blk, limbs, blk_flags, &is_last);
+}
+
+// TMA-streaming form: one producer warp moves the CTA's range through a ring
+// of S shared-memory stages with bulk asynchronous copies (cp.async.bulk,
+// completion tracked by mbarriers); C consumer warps read their vectors from
+// the ring, release the stage at once and add the elements into their
+// digit columns.  The bytes in flight live in shared memory rather than in
+// registers, so a CTA keeps S stages of the input in flight.
+template <int DT, int C, int U, int S>
+__global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_tma(SumArgs a) {
+  constexpr int T = C * 32;          // consumer threads (digit columns)
+  constexpr int NW = C + 1;
+  constexpr int ND = Geometry<DT>::DIGITS;
+  constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
+  constexpr int EPV = 16 / Geometry<DT>::ELEM_BYTES;
+  constexpr int BATCH = T * U;       // vectors per stage
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  int64_t* digits = reinterpret_cast<int64_t*>(smem_raw);                       // ND x T
+  uint4* ring = reinterpret_cast<uint4*>(smem_raw + (size_t)ND * T * 8);        // S x BATCH
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)S * BATCH);       // S
+  uint64_t* empty = full + S;                                                    // S
+  __shared__ int64_t blk[ACC_WORDS];
+  __shared__ uint32_t limbs[ACC_DIGITS];
+  __shared__ uint32_t blk_flags, is_last;
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int64_t G = gridDim.x;
+  const int64_t vb = a.nvec * blockIdx.x / G, ve = a.nvec * (blockIdx.x + 1) / G;
+  const int64_t nv_cta = ve - vb;
+  const int64_t nbatch = (nv_cta + BATCH - 1) / BATCH;
+  const uint4* vx = reinterpret_cast<const uint4*>((const char*)a.x + a.head * Geometry<DT>::ELEM_BYTES);
+
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C);
+    }
+    blk_flags = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  uint32_t flags = 0;
+  if (warp == C) {
+    // ---- producer: one elected lane issues the bulk copies ----
+    if (lane == 0) {
+      bool ok = true;
+      int64_t issued = 0;
+      for (int64_t k = 0; k < nbatch; ++k) {
+        const int s = (int)(k % S);
+        if (k >= S && !mbar_wait(&empty[s], (uint32_t)((k / S - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const int64_t nv = min((int64_t)BATCH, nv_cta - k * BATCH);
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(nv * 16));
+        bulk_copy_g2s(ring + (size_t)s * BATCH, vx + vb + k * BATCH, (uint32_t)(nv * 16), &full[s]);
+        issued = k + 1;
+      }
+      // never leave copies in flight: wait (bounded) for the last ones to land
+      for (int64_t k = (issued > S ? issued - S : 0); k < issued; ++k)
+        ok &= mbar_wait(&full[k % S], (uint32_t)((k / S) & 1));
+      if (!ok) atomicOr(a.status, STATUS_TIMEOUT);
+    }
+  } else {
+    // ---- consumers ----
+    int64_t* col = digits + t;
+#pragma unroll 4
+    for (int i = 0; i < ND; ++i) col[i * T] = 0;
+    uint32_t emax = 0;
+    int reg_left = REG_EVERY;
+    bool ok = true;
+    for (int64_t k = 0; k < nbatch; ++k) {
+      const int s = (int)(k % S);
+      if (!mbar_wait(&full[s], (uint32_t)((k / S) & 1))) {
+        ok = false;
+        break;
+      }
+      const int64_t nv = min((int64_t)BATCH, nv_cta - k * BATCH);
+      const uint4* st = ring + (size_t)s * BATCH;
+      uint4 r[U];
+      if (nv == BATCH) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) r[u] = lds128(st + t + u * T);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) add_vec<DT, T>(col, r[u], emax);
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (t + u * T < nv) r[u] = lds128(st + t + u * T);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (t + u * T < nv) add_vec<DT, T>(col, r[u], emax);
+      }
+      reg_left -= U * EPV;
+      if (reg_left <= 0) {
+        regularise<DT, T>(col);
+        reg_left = REG_EVERY;
+      }
+    }
+    if (!ok && lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
+    if (blockIdx.x == 0 && t < a.head) add_one<DT, T>(col, load_one<DT>(a.x, t), emax);
+    if (blockIdx.x == G - 1 && t < a.tail) add_one<DT, T>(col, load_one<DT>(a.x, a.n - a.tail + t), emax);
+    regularise<DT, T>(col);
+    // consumer thread t owns vectors vb + t + j*T: the same sets as the
+    // register-streaming form, so the same exact rescan applies
+    flags = 24u;
+    if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) flags = rescan_flags<DT, T>(a, vb, ve);
+  }
+  __syncthreads();
+  if (flags) atomicOr(&blk_flags, flags);
+  __syncthreads();
+  finish_cta<DT, T, NW>(a, digits, blk, limbs, blk_flags, &is_last);
+}
+
 // Round a caller-held accumulator (one thread).
 __global__ void round_acc_kernel(const int64_t* acc, int in_dt, int out, int mode, void* result) {
   __shared__ int64_t blk[ACC_WORDS];
@@ -154,11 +276,38 @@ __global__ void round_acc_kernel(const int64_t* acc, int in_dt, int out, int mod
 // ---------------------------------------------------------------------------
 template <int DT>
 struct SumConfig;
+// Streaming form and shape per input format (chosen by measurement):
+//   TMA = 1: sum_kernel_tma<DT, C, TU, S>, (C + 1) warps, S stages of C*32*TU vectors;
+//   TMA = 0: sum_kernel<DT, T, U>, T threads, U vectors per batch.
+#ifndef ES_F64_TMA
+#define ES_F64_TMA 1
+#endif
+#ifndef ES_F64_C
+#define ES_F64_C 8
+#endif
+#ifndef ES_F64_TU
+#define ES_F64_TU 8
+#endif
+#ifndef ES_F64_S
+#define ES_F64_S 2
+#endif
 #ifndef ES_F64_T
 #define ES_F64_T 384
 #endif
 #ifndef ES_F64_U
-#define ES_F64_U 4
+#define ES_F64_U 8
+#endif
+#ifndef ES_F32_TMA
+#define ES_F32_TMA 0
+#endif
+#ifndef ES_F32_C
+#define ES_F32_C 12
+#endif
+#ifndef ES_F32_TU
+#define ES_F32_TU 4
+#endif
+#ifndef ES_F32_S
+#define ES_F32_S 4
 #endif
 #ifndef ES_F32_T
 #define ES_F32_T 512
@@ -166,36 +315,65 @@ struct SumConfig;
 #ifndef ES_F32_U
 #define ES_F32_U 4
 #endif
+#ifndef ES_BF16_TMA
+#define ES_BF16_TMA 0
+#endif
+#ifndef ES_BF16_C
+#define ES_BF16_C 12
+#endif
+#ifndef ES_BF16_TU
+#define ES_BF16_TU 4
+#endif
+#ifndef ES_BF16_S
+#define ES_BF16_S 4
+#endif
 #ifndef ES_BF16_T
 #define ES_BF16_T 512
 #endif
 #ifndef ES_BF16_U
-#define ES_BF16_U 2
+#define ES_BF16_U 4
 #endif
-template <> struct SumConfig<F64> { static constexpr int T = ES_F64_T, U = ES_F64_U; };
-template <> struct SumConfig<F32> { static constexpr int T = ES_F32_T, U = ES_F32_U; };
-template <> struct SumConfig<BF16> { static constexpr int T = ES_BF16_T, U = ES_BF16_U; };
+template <> struct SumConfig<F64> {
+  static constexpr int TMA = ES_F64_TMA, C = ES_F64_C, TU = ES_F64_TU, S = ES_F64_S, T = ES_F64_T, U = ES_F64_U;
+};
+template <> struct SumConfig<F32> {
+  static constexpr int TMA = ES_F32_TMA, C = ES_F32_C, TU = ES_F32_TU, S = ES_F32_S, T = ES_F32_T, U = ES_F32_U;
+};
+template <> struct SumConfig<BF16> {
+  static constexpr int TMA = ES_BF16_TMA, C = ES_BF16_C, TU = ES_BF16_TU, S = ES_BF16_S, T = ES_BF16_T,
+                       U = ES_BF16_U;
+};
 
 template <int DT>
-static cudaError_t launch_sum_t(const SumArgs& a0, int max_ctas, cudaStream_t stream, int* grid_out) {
-  constexpr int T = SumConfig<DT>::T, U = SumConfig<DT>::U;
-  constexpr size_t SMEM = (size_t)Geometry<DT>::DIGITS * T * sizeof(int64_t);
+static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out) {
+  using Cfg = SumConfig<DT>;
+  constexpr int ND = Geometry<DT>::DIGITS;
+  constexpr int THREADS = Cfg::TMA ? (Cfg::C + 1) * 32 : Cfg::T;
+  constexpr int COLS = Cfg::TMA ? Cfg::C * 32 : Cfg::T;
+  constexpr size_t SMEM = Cfg::TMA ? (size_t)ND * COLS * 8 + (size_t)Cfg::S * COLS * Cfg::TU * 16 + 2 * Cfg::S * 8
+                                   : (size_t)ND * COLS * 8;
+  static_assert(((size_t)ND * COLS * 8) % 128 == 0, "ring must start 128-byte aligned");
+  static_assert(SMEM + 1024 <= 232448, "shared memory per CTA");
+  const void* fn;
+  if constexpr (Cfg::TMA) fn = (const void*)sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S>;
+  else fn = (const void*)sum_kernel<DT, Cfg::T, Cfg::U>;
   static bool configured[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    e = cudaFuncSetAttribute(sum_kernel<DT, T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  SumArgs a = a0;
-  // at least two vectors per thread per CTA, at most one CTA per SM
-  int64_t want = (a.nvec + 2 * T - 1) / (2 * T);
-  int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
+  // at least two vectors per column per CTA, at most one CTA per SM
+  const int64_t want = (a.nvec + 2 * COLS - 1) / (2 * COLS);
+  const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
   if (grid_out) *grid_out = grid;
-  sum_kernel<DT, T, U><<<grid, T, SMEM, stream>>>(a);
+  if constexpr (Cfg::TMA)
+    sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S><<<grid, THREADS, SMEM, stream>>>(a);
+  else
+    sum_kernel<DT, Cfg::T, Cfg::U><<<grid, THREADS, SMEM, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -213,8 +391,5 @@ cudaError_t launch_round_acc(const int64_t* acc, int in_dt, int out, int mode, v
   return cudaGetLastError();
 }
 
-int sum_threads_per_cta(int in_dt) {
-  return in_dt == F64 ? SumConfig<F64>::T : (in_dt == F32 ? SumConfig<F32>::T : SumConfig<BF16>::T);
-}
 
 }  // namespace es

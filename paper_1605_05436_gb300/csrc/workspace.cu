@@ -13,6 +13,8 @@ exactsum_status es_workspace_init(exactsum_t h) {
     return es_cuda_fail(h, e, "cudaMalloc(partials)");
   if ((e = cudaMalloc(&h->ticket, 64)) != cudaSuccess) return es_cuda_fail(h, e, "cudaMalloc(ticket)");
   if ((e = cudaMemset(h->ticket, 0, 64)) != cudaSuccess) return es_cuda_fail(h, e, "cudaMemset(ticket)");
+  if ((e = cudaMalloc(&h->dev_status, 64)) != cudaSuccess) return es_cuda_fail(h, e, "cudaMalloc(status)");
+  if ((e = cudaMemset(h->dev_status, 0, 64)) != cudaSuccess) return es_cuda_fail(h, e, "cudaMemset(status)");
   if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return es_cuda_fail(h, e, "cudaStreamCreate");
   for (int i = 0; i < 2; ++i) {
@@ -32,6 +34,7 @@ exactsum_status es_workspace_init(exactsum_t h) {
 void es_workspace_free(exactsum_t h) {
   cudaFree(h->partials);
   cudaFree(h->ticket);
+  cudaFree(h->dev_status);
   for (int i = 0; i < 2; ++i) {
     if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
     if (h->ev_consumed[i]) cudaEventDestroy(h->ev_consumed[i]);
@@ -88,6 +91,7 @@ exactsum_status es_sum_host_pipelined(exactsum_t h, const void* h_x, int64_t n, 
     a.acc = h->host_acc;
     a.partials = h->partials;
     a.ticket = h->ticket;
+    a.status = h->dev_status;
     if ((e = es::launch_sum(in, a, h->max_ctas, stream, nullptr)) != cudaSuccess)
       return es_cuda_fail(h, e, "accumulate kernel launch");
     if ((e = cudaEventRecord(h->ev_consumed[b], stream)) != cudaSuccess)
