@@ -288,6 +288,38 @@ const char* exactsum_server_last_error(exactsum_server_t s);
  * the engine. */
 exactsum_status exactsum_server_destroy(exactsum_server_t s);
 
+/* ---------------------------------------------------------------------- */
+/* Allocation-free segmented sum                                           */
+/* (no counterpart in the paper: a deployment variant of                   */
+/* exactsum_segmented_sum)                                                 */
+/* ---------------------------------------------------------------------- */
+
+#define EXACTSUM_NOALLOC_MAX_SEGMENTS 2048
+
+/* The same results as exactsum_segmented_sum, for callers that cannot
+ * allocate device memory -- code that must not allocate while a stream is
+ * being captured, programs whose device memory belongs to a fixed pool or to
+ * another framework's allocator, hosts that forbid allocation after
+ * start-up.  It needs no handle and calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch is one fixed array of about 3.4 MB in
+ * the library's own device memory, present on every GPU that loads the
+ * library until the process exits.
+ *   - Runs on the calling thread's current device; arguments as in
+ *     exactsum_segmented_sum (device input, device int64 offsets, device
+ *     results).
+ *   - num_segments must not exceed EXACTSUM_NOALLOC_MAX_SEGMENTS; a larger
+ *     call returns EXACTSUM_EINVAL (message in exactsum_last_error(NULL))
+ *     and enqueues nothing.  Inputs up to 512 GiB are covered.
+ *   - All calls share the one scratch array and each call clears the parts
+ *     that must start at zero: calls whose work overlaps on the GPU race,
+ *     so order them (for example on one stream).
+ *   - The first call on each device looks up the scratch array's device
+ *     address; make that first call before any stream capture starts.
+ *   - Asynchronous on `stream`; no graph capture of its own. */
+exactsum_status exactsum_segmented_sum_noalloc(const void* d_x, const int64_t* d_offsets,
+                                               int64_t num_segments, int in_dtype, int out_dtype,
+                                               int mode, void* d_results, exactsum_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,6 +58,7 @@ _SIGNATURES = {
     "exactsum_server_drain": [_vp, _i64],
     "exactsum_server_stats": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "exactsum_server_destroy": [_vp],
+    "exactsum_segmented_sum_noalloc": [_vp, _vp, _i64, _int, _int, _int, _vp, _vp],
 }
 OPTIONAL_SIGNATURES: dict = {}
 
@@ -193,6 +194,15 @@ def exactsum_device_status(handle) -> int:
 
 
 STATUS_BAD_OFFSETS, STATUS_MAP_OVERFLOW = 1, 2
+NOALLOC_MAX_SEGMENTS = 2048
+
+
+def exactsum_segmented_sum_noalloc(d_x, d_offsets, num_segments, in_dtype, out_dtype, mode, d_results,
+                                   stream) -> None:
+    """Segmented sum that allocates nothing (fixed scratch inside the
+    library; at most NOALLOC_MAX_SEGMENTS segments; overlapping calls race)."""
+    _check(library().exactsum_segmented_sum_noalloc(d_x, d_offsets, num_segments, in_dtype, out_dtype, mode,
+                                                    d_results, stream), None)
 
 
 class exactsum_completion(ctypes.Structure):

@@ -26,6 +26,10 @@ static exactsum_status fail(exactsum_t h, exactsum_status st, const char* fmt, .
   return st;
 }
 
+// Message for entry points that have no handle (reported by
+// exactsum_last_error(NULL) on the calling thread).
+void es_set_detached_error(const char* msg) { g_null_handle_error = msg; }
+
 exactsum_status es_cuda_fail(exactsum_t h, cudaError_t e, const char* what) {
   return fail(h, EXACTSUM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
