@@ -43,7 +43,13 @@ template <> struct Geometry<F64> {
   static constexpr int RADIX_BITS = 32;
   static constexpr int DIGITS = 66;           // per-thread digits
   static constexpr int ELEM_BYTES = 8;
-  static constexpr int REG_EVERY = 1024;      // adds between regularisations (< 2^11)
+#ifndef ES_F64_REG_EVERY
+#define ES_F64_REG_EVERY 1984
+#endif
+  // adds between regularisations: after one, |digit| <= 2^31 + 2^21, and each
+  // add changes a digit by less than 2^52, so up to 2047 adds stay below 2^63
+  // (callers check after each batch of at most 16 adds, plus 2 scalar adds)
+  static constexpr int REG_EVERY = ES_F64_REG_EVERY;
   static constexpr uint32_t EXP_SPECIAL = 0x7FF;
 };
 template <> struct Geometry<F32> {
@@ -79,13 +85,30 @@ __host__ __device__ constexpr int unit_exp_of(int dt) {
 // the plain load / add / store.)
 __device__ __forceinline__ void digit_add(int64_t* d, int64_t v) { *d += v; }
 
+#ifndef ES_DECODE_V2
+#define ES_DECODE_V2 0
+#endif
+#ifndef ES_P_FUSED
+#define ES_P_FUSED 0
+#endif
+
+// Element decode and digit addition with the biased exponent E already
+// extracted.  The hidden bit (set iff E >= 1) is taken from bit 11 (FP64) or
+// bit 8 (FP32) of E + all-ones, moved into place by a multiply, so that it
+// costs one integer multiply-add (FMA pipe) and one three-input logic op.
 template <int STRIDE>
-__device__ __forceinline__ void add_f64(int64_t* __restrict__ col, uint32_t lo, uint32_t hi,
-                                        uint32_t& emax) {
-  const uint32_t E = (hi >> 20) & 0x7FFu;
-  emax = max(emax, E);
-  const uint32_t mhi = (hi & 0xFFFFFu) | (E != 0u ? 0x100000u : 0u);  // bits 32..52 of m
+__device__ __forceinline__ void add_f64_e(int64_t* __restrict__ col, uint32_t lo, uint32_t hi, uint32_t E) {
+#if ES_DECODE_V2
+  const uint32_t t = E * 512u + (0x7FFu << 9);          // bit 20 = (E >= 1); bits > 20 clear
+  const uint32_t mhi = (hi & 0xFFFFFu) | (t & ~0xFFFFFu);  // bits 32..52 of m
+#else
+  const uint32_t mhi = (hi & 0xFFFFFu) | (E != 0u ? 0x100000u : 0u);
+#endif
+#if ES_P_FUSED
+  const uint32_t p = (uint32_t)max((int)E - 1, 0);
+#else
   const uint32_t p = max(E, 1u) - 1u;
+#endif
   // v = m << (p & 31) as three 32-bit words w2:w1:w0 (funnel shifts use p & 31)
   const uint32_t w0 = __funnelshift_l(0u, lo, p);
   const uint32_t w1 = __funnelshift_l(lo, mhi, p);
@@ -99,13 +122,46 @@ __device__ __forceinline__ void add_f64(int64_t* __restrict__ col, uint32_t lo, 
 }
 
 template <int STRIDE>
+__device__ __forceinline__ void add_f64(int64_t* __restrict__ col, uint32_t lo, uint32_t hi,
+                                        uint32_t& emax) {
+  const uint32_t E = (hi >> 20) & 0x7FFu;
+  emax = max(emax, E);
+  add_f64_e<STRIDE>(col, lo, hi, E);
+}
+
+template <int STRIDE>
+__device__ __forceinline__ void add_f32_e(int64_t* __restrict__ col, uint32_t w, uint32_t E) {
+#if ES_DECODE_V2
+  const uint32_t t = E * 32768u + (0xFFu << 15);         // bit 23 = (E >= 1); bits > 23 clear
+  const uint32_t m = (w & 0x7FFFFFu) | (t & ~0x7FFFFFu);
+  const uint32_t p = (uint32_t)max((int)E - 1, 0);
+#else
+  const uint32_t m = (w & 0x7FFFFFu) | (E != 0u ? 0x800000u : 0u);
+  const uint32_t p = max(E, 1u) - 1u;
+#endif
+  const int32_t s = (int32_t)w >> 31;
+  const int32_t v = ((int32_t)(m << (p & 7u)) ^ s) - s;  // |v| < 2^31
+  digit_add(col + (p >> 3) * STRIDE, (int64_t)v);
+}
+
+template <int STRIDE>
 __device__ __forceinline__ void add_f32(int64_t* __restrict__ col, uint32_t w, uint32_t& emax) {
   const uint32_t E = (w >> 23) & 0xFFu;
   emax = max(emax, E);
-  const uint32_t m = (w & 0x7FFFFFu) | (E != 0u ? 0x800000u : 0u);
+  add_f32_e<STRIDE>(col, w, E);
+}
+
+template <int STRIDE>
+__device__ __forceinline__ void add_bf16_e(int64_t* __restrict__ col, uint32_t h, uint32_t E) {
+#if ES_DECODE_V2
+  const uint32_t m = (h & 0x7Fu) | (min(E, 1u) * 128u);
+  const uint32_t p = (uint32_t)max((int)E - 1, 0);
+#else
+  const uint32_t m = (h & 0x7Fu) | (E != 0u ? 0x80u : 0u);
   const uint32_t p = max(E, 1u) - 1u;
-  const int32_t s = (int32_t)w >> 31;
-  const int32_t v = ((int32_t)(m << (p & 7u)) ^ s) - s;  // |v| < 2^31
+#endif
+  const int32_t s = -(int32_t)((h >> 15) & 1u);
+  const int32_t v = ((int32_t)(m << (p & 7u)) ^ s) - s;  // |v| < 2^15
   digit_add(col + (p >> 3) * STRIDE, (int64_t)v);
 }
 
@@ -113,33 +169,41 @@ template <int STRIDE>
 __device__ __forceinline__ void add_bf16(int64_t* __restrict__ col, uint32_t h, uint32_t& emax) {
   const uint32_t E = (h >> 7) & 0xFFu;
   emax = max(emax, E);
-  const uint32_t m = (h & 0x7Fu) | (E != 0u ? 0x80u : 0u);
-  const uint32_t p = max(E, 1u) - 1u;
-  const int32_t s = -(int32_t)((h >> 15) & 1u);
-  const int32_t v = ((int32_t)(m << (p & 7u)) ^ s) - s;  // |v| < 2^15
-  digit_add(col + (p >> 3) * STRIDE, (int64_t)v);
+  add_bf16_e<STRIDE>(col, h, E);
 }
 
-// Add all elements held in one 16-byte vector.
+// Add all elements held in one 16-byte vector.  The exponent maximum is
+// updated with three-input maxima, once per vector.
 template <int DT, int STRIDE>
 __device__ __forceinline__ void add_vec(int64_t* __restrict__ col, const uint4& v, uint32_t& emax) {
   if constexpr (DT == F64) {
-    add_f64<STRIDE>(col, v.x, v.y, emax);
-    add_f64<STRIDE>(col, v.z, v.w, emax);
+    const uint32_t e0 = (v.y >> 20) & 0x7FFu, e1 = (v.w >> 20) & 0x7FFu;
+    emax = __vimax3_u32(emax, e0, e1);
+    add_f64_e<STRIDE>(col, v.x, v.y, e0);
+    add_f64_e<STRIDE>(col, v.z, v.w, e1);
   } else if constexpr (DT == F32) {
-    add_f32<STRIDE>(col, v.x, emax);
-    add_f32<STRIDE>(col, v.y, emax);
-    add_f32<STRIDE>(col, v.z, emax);
-    add_f32<STRIDE>(col, v.w, emax);
+    const uint32_t e0 = (v.x >> 23) & 0xFFu, e1 = (v.y >> 23) & 0xFFu;
+    const uint32_t e2 = (v.z >> 23) & 0xFFu, e3 = (v.w >> 23) & 0xFFu;
+    emax = __vimax3_u32(__vimax3_u32(emax, e0, e1), e2, e3);
+    add_f32_e<STRIDE>(col, v.x, e0);
+    add_f32_e<STRIDE>(col, v.y, e1);
+    add_f32_e<STRIDE>(col, v.z, e2);
+    add_f32_e<STRIDE>(col, v.w, e3);
   } else {
-    add_bf16<STRIDE>(col, v.x & 0xFFFFu, emax);
-    add_bf16<STRIDE>(col, v.x >> 16, emax);
-    add_bf16<STRIDE>(col, v.y & 0xFFFFu, emax);
-    add_bf16<STRIDE>(col, v.y >> 16, emax);
-    add_bf16<STRIDE>(col, v.z & 0xFFFFu, emax);
-    add_bf16<STRIDE>(col, v.z >> 16, emax);
-    add_bf16<STRIDE>(col, v.w & 0xFFFFu, emax);
-    add_bf16<STRIDE>(col, v.w >> 16, emax);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t e[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      e[2 * k] = (w[k] >> 7) & 0xFFu;
+      e[2 * k + 1] = (w[k] >> 23) & 0xFFu;
+    }
+    emax = __vimax3_u32(__vimax3_u32(emax, e[0], e[1]), __vimax3_u32(e[2], e[3], e[4]),
+                        __vimax3_u32(e[5], e[6], e[7]));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      add_bf16_e<STRIDE>(col, w[k] & 0xFFFFu, e[2 * k]);
+      add_bf16_e<STRIDE>(col, w[k] >> 16, e[2 * k + 1]);
+    }
   }
 }
 

@@ -286,7 +286,7 @@ struct SumConfig;
 #define ES_F64_C 8
 #endif
 #ifndef ES_F64_TU
-#define ES_F64_TU 8
+#define ES_F64_TU 11
 #endif
 #ifndef ES_F64_S
 #define ES_F64_S 2
@@ -328,7 +328,7 @@ struct SumConfig;
 #define ES_BF16_S 4
 #endif
 #ifndef ES_BF16_T
-#define ES_BF16_T 512
+#define ES_BF16_T 768
 #endif
 #ifndef ES_BF16_U
 #define ES_BF16_U 4
