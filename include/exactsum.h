@@ -252,10 +252,14 @@ typedef struct {
  *     batching: every step carries one chunk of every resident request, in
  *     one kernel, so requests that arrive later join at the next step).
  *   tile_elems: elements per warp work unit (multiple of 64 dividing
- *     chunk_elems). */
+ *     chunk_elems).
+ *   max_steps_per_request: if > 0, a request's chunk grows to
+ *     ceil(n / max_steps_per_request) (whole tiles) when that is larger than
+ *     chunk_elems, so that no request needs more than that many steps; 0
+ *     keeps the fixed chunk. */
 exactsum_status exactsum_server_create(exactsum_server_t* out, int device, int max_slots,
                                        int64_t mem_budget_bytes, int64_t chunk_elems,
-                                       int64_t tile_elems);
+                                       int64_t tile_elems, int max_steps_per_request);
 
 /* Queue a request: the exact sum of x[0..n) (in_dtype) rounded to
  * out_dtype under mode.  x_on_host = 0: x is device memory that must stay

@@ -52,7 +52,7 @@ _SIGNATURES = {
     "exactsum_tuning_save": [_vp, ctypes.c_char_p],
     "exactsum_tuning_load": [_vp, ctypes.c_char_p],
     "exactsum_device_status": [_vp, ctypes.POINTER(_i64)],
-    "exactsum_server_create": [ctypes.POINTER(_vp), _int, _int, _i64, _i64, _i64],
+    "exactsum_server_create": [ctypes.POINTER(_vp), _int, _int, _i64, _i64, _i64, _int],
     "exactsum_server_submit": [_vp, _vp, _i64, _int, _int, _int, _int, ctypes.POINTER(ctypes.c_uint64)],
     "exactsum_server_poll": [_vp, _vp, _int, ctypes.POINTER(_int)],
     "exactsum_server_drain": [_vp, _i64],
@@ -218,10 +218,10 @@ def _check_server(status: int, server) -> None:
 
 
 def exactsum_server_create(device: int, max_slots: int, mem_budget_bytes: int, chunk_elems: int,
-                           tile_elems: int) -> int:
+                           tile_elems: int, max_steps_per_request: int = 0) -> int:
     h = _vp()
     _check_server(library().exactsum_server_create(ctypes.byref(h), device, max_slots, mem_budget_bytes,
-                                                   chunk_elems, tile_elems), None)
+                                                   chunk_elems, tile_elems, max_steps_per_request), None)
     return h.value
 
 

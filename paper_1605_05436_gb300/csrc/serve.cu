@@ -10,9 +10,12 @@
 //                retire steps whose completion event has fired
 //   poll()    <- completion records (id, status, result bits, timestamps)
 //
-// Up to two steps are in flight, so the host prepares step k+1 while step k
-// runs.  A request's partial sum stays in its device slot accumulator from
-// its first chunk to its last.
+// Up to SERVE_STEPS_IN_FLIGHT steps are in flight, so the host prepares the
+// next steps while one runs.  A request's partial sum stays in its device
+// slot accumulator from its first chunk to its last.  A request's chunk is
+// the larger of the engine's chunk and 1/max_steps of the request, so that
+// a large request finishes in at most max_steps steps however many others
+// share them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,6 +54,7 @@ struct Req {
   int64_t pos = 0;           // elements issued so far
   int slot = -1;
   bool fresh = true;         // staged copy not yet waited on by the compute stream
+  int64_t chunk = 0;         // elements per step for this request
   void* staged = nullptr;
   cudaEvent_t ready = nullptr;
   int64_t submit_ns = 0, admit_ns = 0;
@@ -68,13 +72,15 @@ struct StepBuf {
 
 }  // namespace
 
+constexpr int SERVE_STEPS_IN_FLIGHT = 2;
+
 struct exactsum_server {
   int device = 0, num_sms = 0, max_slots = 0;
-  int64_t budget = 0, chunk = 0, tile = 0;
+  int64_t budget = 0, chunk = 0, tile = 0, max_steps = 0;
   cudaStream_t compute = nullptr, copy = nullptr;
   int64_t* slot_acc = nullptr;
   uint64_t* d_results = nullptr;
-  StepBuf bufs[2];
+  StepBuf bufs[SERVE_STEPS_IN_FLIGHT];
   int64_t step_seq = 0;
 
   std::thread th;
@@ -195,6 +201,13 @@ bool admit(exactsum_server* s) {
       r->slot = free_slot;
     }
     r->admit_ns = now_ns();
+    r->chunk = s->chunk;
+    if (s->max_steps > 0) {
+      // at most max_steps steps: round the per-step share up to whole tiles
+      const int64_t share = (r->n + s->max_steps - 1) / s->max_steps;
+      const int64_t tiles = (share + s->tile - 1) / s->tile;
+      r->chunk = std::max(s->chunk, tiles * s->tile);
+    }
     s->slots[r->slot] = r;
     s->mem_used += r->bytes;
     if (r->host) {
@@ -238,7 +251,7 @@ bool launch_step(exactsum_server* s) {
     const int i = (s->rr + k) % s->max_slots;
     Req* r = s->slots[i];
     if (!r || r->pos >= r->n) continue;
-    const int64_t len = std::min(s->chunk, r->n - r->pos);
+    const int64_t len = std::min(r->chunk, r->n - r->pos);
     es::ServeItem& it = b->h_block->items[nitems];
     it.x = r->xd + r->pos * elem_bytes(r->in);
     it.len = len;
@@ -296,7 +309,8 @@ void scheduler(exactsum_server* s) {
     progress |= launch_step(s);
     if (s->failed.load()) break;
     if (!progress) {
-      bool busy = s->bufs[0].busy || s->bufs[1].busy;
+      bool busy = false;
+      for (auto& b : s->bufs) busy |= b.busy;
       if (!busy) {
         bool any_active = false;
         for (Req* r : s->slots) any_active |= (r != nullptr);
@@ -337,11 +351,12 @@ void server_free(exactsum_server* s) {
 extern "C" {
 
 exactsum_status exactsum_server_create(exactsum_server_t* out, int device, int max_slots,
-                                       int64_t mem_budget_bytes, int64_t chunk_elems, int64_t tile_elems) {
+                                       int64_t mem_budget_bytes, int64_t chunk_elems, int64_t tile_elems,
+                                       int max_steps_per_request) {
   if (!out) return EXACTSUM_EINVAL;
   *out = nullptr;
   if (max_slots < 1 || max_slots > es::SERVE_MAX_ITEMS || mem_budget_bytes <= 0 || chunk_elems < 1 ||
-      tile_elems < 64 || tile_elems % 64 || chunk_elems % tile_elems)
+      tile_elems < 64 || tile_elems % 64 || chunk_elems % tile_elems || max_steps_per_request < 0)
     return EXACTSUM_EINVAL;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return EXACTSUM_ECUDA;
@@ -355,6 +370,7 @@ exactsum_status exactsum_server_create(exactsum_server_t* out, int device, int m
   s->budget = mem_budget_bytes;
   s->chunk = chunk_elems;
   s->tile = tile_elems;
+  s->max_steps = max_steps_per_request;
   s->slots.assign(max_slots, nullptr);
   bool ok = es::serve_configure() == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) == cudaSuccess;

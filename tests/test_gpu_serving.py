@@ -46,8 +46,9 @@ def pools():
             es.BF16: (p16, G.to_device(p16, es.BF16, DEV))}
 
 
-def test_mixed_requests_match_oracle(pools):
-    server = es.exactsum_server_create(0, 64, 1 << 30, 1 << 16, 1 << 12)
+@pytest.mark.parametrize("max_steps", [0, 3])
+def test_mixed_requests_match_oracle(pools, max_steps):
+    server = es.exactsum_server_create(0, 64, 1 << 30, 1 << 16, 1 << 12, max_steps)
     try:
         rng = np.random.default_rng(1)
         sizes = [0, 1, 2, 3, 63, 64, 65, 4095, 4096, 4097, 65535, 65536, 65537, 300_001, 1 << 21]
