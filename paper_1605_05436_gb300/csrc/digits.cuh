@@ -258,6 +258,87 @@ __device__ __forceinline__ int64_t digit32(const int64_t* __restrict__ col, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// BF16 with 32-bit digits.  A BF16 element adds less than 2^15 to one
+// radix-2^8 digit, so an int32 digit regularised to |D| <= 2^7 takes 65,000
+// more additions before it could overflow: half the shared-memory traffic
+// and a quarter of the column footprint of the int64 form.
+// ---------------------------------------------------------------------------
+template <int STRIDE>
+__device__ __forceinline__ void add_bf16_e(int32_t* __restrict__ col, uint32_t h, uint32_t E) {
+  const uint32_t m = (h & 0x7Fu) | (E != 0u ? 0x80u : 0u);
+  const uint32_t p = max(E, 1u) - 1u;
+  const int32_t s = -(int32_t)((h >> 15) & 1u);
+  const int32_t v = ((int32_t)(m << (p & 7u)) ^ s) - s;  // |v| < 2^15
+  col[(p >> 3) * STRIDE] += v;
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_vec(int32_t* __restrict__ col, const uint4& v, uint32_t& emax) {
+  static_assert(DT == BF16, "32-bit digit columns hold BF16 sums only");
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint32_t e[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    e[2 * k] = (w[k] >> 7) & 0xFFu;
+    e[2 * k + 1] = (w[k] >> 23) & 0xFFu;
+  }
+  emax = __vimax3_u32(__vimax3_u32(emax, e[0], e[1]), __vimax3_u32(e[2], e[3], e[4]),
+                      __vimax3_u32(e[5], e[6], e[7]));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    add_bf16_e<STRIDE>(col, w[k] & 0xFFFFu, e[2 * k]);
+    add_bf16_e<STRIDE>(col, w[k] >> 16, e[2 * k + 1]);
+  }
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_one(int32_t* __restrict__ col, uint64_t bits, uint32_t& emax) {
+  static_assert(DT == BF16, "32-bit digit columns hold BF16 sums only");
+  const uint32_t h = (uint32_t)bits & 0xFFFFu;
+  const uint32_t E = (h >> 7) & 0xFFu;
+  emax = max(emax, E);
+  add_bf16_e<STRIDE>(col, h, E);
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void regularise(int32_t* __restrict__ col) {
+  static_assert(DT == BF16, "32-bit digit columns hold BF16 sums only");
+  constexpr int ND = Geometry<DT>::DIGITS;
+  int32_t carry = 0;
+#pragma unroll 4
+  for (int i = 0; i < ND - 1; ++i) {
+    const int32_t v = col[i * STRIDE] + carry;
+    const int32_t c = (v + 128) >> 8;
+    col[i * STRIDE] = v - (c << 8);
+    carry = c;
+  }
+  col[(ND - 1) * STRIDE] += carry;
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ int64_t digit32(const int32_t* __restrict__ col, int i) {
+  static_assert(DT == BF16, "32-bit digit columns hold BF16 sums only");
+  constexpr int ND = Geometry<DT>::DIGITS;
+  int64_t v = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int j = 4 * i + k;
+    if (j < ND) v += (int64_t)col[j * STRIDE] * ((int64_t)1 << (8 * k));
+  }
+  return v;
+}
+
+// Additions between regularisations for a digit type.
+template <int DT, typename D>
+struct RegEvery {
+  static constexpr int value = Geometry<DT>::REG_EVERY;
+};
+template <>
+struct RegEvery<BF16, int32_t> {
+  static constexpr int value = 60000;  // (2^31 - 2^7 - 2^23) / 2^15 > 65,000
+};
+
 // Classify one element for the special-value and signed-zero counters.
 // flags bit 0: NaN, bit 1: +Inf, bit 2: -Inf, bit 3: not +0, bit 4: not -0.
 template <int DT>

@@ -44,12 +44,12 @@ __device__ __forceinline__ int64_t warp_sum(int64_t v) {
 // is the group's first vector) also prefetches the group's batch
 // ES_PREFETCH_BATCHES ahead into L2, clamped to [p, group_end), so that more
 // bytes are in flight than the registers can hold.
-template <int DT, int SSTRIDE, int STEP, int U>
-__device__ __forceinline__ void stream_add(int64_t* __restrict__ col, const uint4* __restrict__ p,
+template <int DT, int SSTRIDE, int STEP, int U, typename D>
+__device__ __forceinline__ void stream_add(D* __restrict__ col, const uint4* __restrict__ p,
                                            int64_t cnt, uint32_t& emax, int& reg_left, int idx,
                                            const uint4* group_end) {
   constexpr int EPV = 16 / Geometry<DT>::ELEM_BYTES;
-  constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
+  constexpr int REG_EVERY = RegEvery<DT, D>::value;
   constexpr int64_t PER = (int64_t)STEP * U;
   constexpr int PD = ES_PREFETCH_BATCHES;
   const int64_t nb = cnt / U;

@@ -46,16 +46,18 @@ __device__ uint32_t rescan_flags(const SumArgs& a, int64_t vb, int64_t ve) {
 // CTA merge and grid merge, shared by both single-array kernels.  Called by
 // every thread of the CTA after its flags are in blk_flags and a barrier.
 // TC threads own digit columns (digit-major, stride TC); NW warps take part.
-template <int DT, int TC, int NW>
-__device__ __forceinline__ void finish_cta(const SumArgs& a, int64_t* digits, int64_t* blk, uint32_t* limbs,
+template <int DT, int TC, int NW, typename D>
+__device__ __forceinline__ void finish_cta(const SumArgs& a, D* cols, int64_t* blk, uint32_t* limbs,
                                            uint32_t blk_flags, uint32_t* is_last) {
-  static_assert(Geometry<DT>::DIGITS * TC >= NW * ACC_WORDS, "digit area reused for the grid merge");
+  static_assert(Geometry<DT>::DIGITS * TC * sizeof(D) >= NW * ACC_WORDS * sizeof(int64_t),
+                "digit area reused for the grid merge");
+  int64_t* digits = reinterpret_cast<int64_t*>(cols);  // scratch once the columns are merged
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t G = gridDim.x;
   // ---- CTA merge: sum the columns' digits, carry-free ----
   for (int i = warp; i < ACC_DIGITS; i += NW) {
     int64_t s = 0;
-    for (int j = lane; j < TC; j += 32) s += digit32<DT, TC>(digits + j, i);
+    for (int j = lane; j < TC; j += 32) s += digit32<DT, TC>(cols + j, i);
     s = warp_sum(s);
     if (lane == 0) blk[i] = s;
   }
@@ -101,20 +103,22 @@ __device__ __forceinline__ void finish_cta(const SumArgs& a, int64_t* digits, in
 }
 
 // Register-streaming form: every thread loads its own vectors (16-byte
-// read-only loads, double buffered) and owns one digit column.
-template <int DT, int T, int U>
+// read-only loads, double buffered) and owns one digit column of type D
+// (int64, or int32 for BF16).
+template <int DT, int T, int U, typename D>
 __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   constexpr int ND = Geometry<DT>::DIGITS;
-  constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
+  constexpr int REG_EVERY = RegEvery<DT, D>::value;
   constexpr int NW = T / 32;
 
-  extern __shared__ int64_t digits[];  // ND x T
+  extern __shared__ int64_t smem_digits[];  // ND x T digits of type D
+  D* digits = reinterpret_cast<D*>(smem_digits);
   __shared__ int64_t blk[ACC_WORDS];
   __shared__ uint32_t limbs[ACC_DIGITS];
   __shared__ uint32_t blk_flags, is_last;
 
   const int t = threadIdx.x;
-  int64_t* col = digits + t;
+  D* col = digits + t;
 #pragma unroll 4
   for (int i = 0; i < ND; ++i) col[i * T] = 0;
   if (t == 0) blk_flags = 0;
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   __syncthreads();
   if (flags) atomicOr(&blk_flags, flags);
   __syncthreads();
-  finish_cta<DT, T, NW>(a, digits, blk, limbs, blk_flags, &is_last);
+  finish_cta<DT, T, NW, D>(a, digits, blk, limbs, blk_flags, &is_last);
 }
 
 // TMA-streaming form: one producer warp moves the CTA's range through a ring
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_tma(SumArgs a) {
   __syncthreads();
   if (flags) atomicOr(&blk_flags, flags);
   __syncthreads();
-  finish_cta<DT, T, NW>(a, digits, blk, limbs, blk_flags, &is_last);
+  finish_cta<DT, T, NW, int64_t>(a, digits, blk, limbs, blk_flags, &is_last);
 }
 
 // Round a caller-held accumulator (one thread).
@@ -333,15 +337,25 @@ struct SumConfig;
 #ifndef ES_BF16_U
 #define ES_BF16_U 4
 #endif
+#ifndef ES_BF16_I32
+#define ES_BF16_I32 1
+#endif
 template <> struct SumConfig<F64> {
   static constexpr int TMA = ES_F64_TMA, C = ES_F64_C, TU = ES_F64_TU, S = ES_F64_S, T = ES_F64_T, U = ES_F64_U;
+  using Digit = int64_t;
 };
 template <> struct SumConfig<F32> {
   static constexpr int TMA = ES_F32_TMA, C = ES_F32_C, TU = ES_F32_TU, S = ES_F32_S, T = ES_F32_T, U = ES_F32_U;
+  using Digit = int64_t;
 };
 template <> struct SumConfig<BF16> {
   static constexpr int TMA = ES_BF16_TMA, C = ES_BF16_C, TU = ES_BF16_TU, S = ES_BF16_S, T = ES_BF16_T,
                        U = ES_BF16_U;
+#if ES_BF16_I32
+  using Digit = int32_t;
+#else
+  using Digit = int64_t;
+#endif
 };
 
 template <int DT>
@@ -350,13 +364,15 @@ static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t str
   constexpr int ND = Geometry<DT>::DIGITS;
   constexpr int THREADS = Cfg::TMA ? (Cfg::C + 1) * 32 : Cfg::T;
   constexpr int COLS = Cfg::TMA ? Cfg::C * 32 : Cfg::T;
+  using D = typename Cfg::Digit;
+  static_assert(!Cfg::TMA || sizeof(D) == 8, "the TMA form keeps int64 digit columns");
   constexpr size_t SMEM = Cfg::TMA ? (size_t)ND * COLS * 8 + (size_t)Cfg::S * COLS * Cfg::TU * 16 + 2 * Cfg::S * 8
-                                   : (size_t)ND * COLS * 8;
-  static_assert(((size_t)ND * COLS * 8) % 128 == 0, "ring must start 128-byte aligned");
+                                   : (size_t)ND * COLS * sizeof(D);
+  static_assert(!Cfg::TMA || ((size_t)ND * COLS * 8) % 128 == 0, "ring must start 128-byte aligned");
   static_assert(SMEM + 1024 <= 232448, "shared memory per CTA");
   const void* fn;
   if constexpr (Cfg::TMA) fn = (const void*)sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S>;
-  else fn = (const void*)sum_kernel<DT, Cfg::T, Cfg::U>;
+  else fn = (const void*)sum_kernel<DT, Cfg::T, Cfg::U, D>;
   static bool configured[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -373,7 +389,7 @@ static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t str
   if constexpr (Cfg::TMA)
     sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S><<<grid, THREADS, SMEM, stream>>>(a);
   else
-    sum_kernel<DT, Cfg::T, Cfg::U><<<grid, THREADS, SMEM, stream>>>(a);
+    sum_kernel<DT, Cfg::T, Cfg::U, D><<<grid, THREADS, SMEM, stream>>>(a);
   return cudaGetLastError();
 }
 

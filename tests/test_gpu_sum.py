@@ -118,21 +118,37 @@ def test_signed_zero_rules():
                 assert gpu_sum(bits, es.F64, es.F64, m) == oracle.exact_sum(bits, es.F64, es.F64, m, 4), (n, pattern, m)
 
 
-def test_regularisation_bound():
-    """Adversarial inputs at the deferred-carry headroom: every element puts the
-    largest possible high part (m = 2^53 - 1 at offset 31) into one digit, all
-    of the same sign, then alternating."""
-    n = (1 << 22) + 3
-    v = np.uint64((1024 << 52) | ((1 << 52) - 1))  # p = 1023 = 32*31 + 31
-    bits = np.full(n, v, dtype=np.uint64)
-    assert gpu_sum(bits, es.F64, es.F64, es.RNE) == oracle.exact_sum(bits, threads=8)
-    bits[1::2] ^= np.uint64(1 << 63)
-    assert gpu_sum(bits, es.F64, es.F64, es.RNE) == oracle.exact_sum(bits, threads=8)
-    # the FP32 / BF16 analogues: largest mantissa at the largest offset
-    b32 = np.full(n, (8 << 23) | 0x7FFFFF, dtype=np.uint32)  # p = 7
-    assert gpu_sum(b32, es.F32, es.F64, es.RNE) == oracle.exact_sum(b32, es.F32, es.F64, es.RNE, 8)
-    b16 = np.full(n, (8 << 7) | 0x7F, dtype=np.uint16)
-    assert gpu_sum(b16, es.BF16, es.F64, es.RNE) == oracle.exact_sum(b16, es.BF16, es.F64, es.RNE, 8)
+def _constant_device(bits_value: int, n: int, dt: int):
+    """n copies of one bit pattern, filled on the device (no host copy)."""
+    signed = G.NP_SIGNED[dt](np.array([bits_value], dtype=G.NP_UNSIGNED[dt]).view(G.NP_SIGNED[dt])[0])
+    return torch.full((n,), int(signed), dtype=G.torch_bits_dtype(dt), device=DEV)
+
+
+@pytest.mark.parametrize("dt,n", [(es.F64, (1 << 27) + 3), (es.F32, (1 << 28) + 5), (es.BF16, (1 << 34) + 7)])
+def test_regularisation_bound(dt, n):
+    """Adversarial inputs at the deferred-carry headroom: every element adds
+    the largest possible value to one digit (mantissa all ones at the
+    largest in-digit offset), all of one sign and then with alternating
+    signs.  n is large enough that each thread regularises mid-stream.  The
+    exact sums are closed forms (n * x and x), rounded by the oracle."""
+    if dt == es.F64:
+        v, unit, m, p = (1024 << 52) | ((1 << 52) - 1), -1074, (1 << 53) - 1, 1023   # p = 32*31 + 31
+    elif dt == es.F32:
+        v, unit, m, p = (8 << 23) | 0x7FFFFF, -149, (1 << 24) - 1, 7                # p & 7 == 7
+    else:
+        v, unit, m, p = (8 << 7) | 0x7F, -133, (1 << 8) - 1, 7
+    sign = 1 << (8 * es.ITEMSIZE[dt] - 1)
+    x = _constant_device(v, n, dt)
+    for o in (dt, es.F64):
+        r = es.exact_sum(x, o, es.RNE)
+        torch.cuda.synchronize()
+        assert G.result_bits(r, o)[0] == oracle.round_value(n * (m << p), unit, o, es.RNE), o
+    neg = _constant_device(v | sign, 1, dt)
+    x[1::2] = neg[0]  # alternate signs: n is odd, so the sum is x itself
+    r = es.exact_sum(x, dt, es.RNE)
+    torch.cuda.synchronize()
+    assert G.result_bits(r, dt)[0] == v
+    del x
 
 
 def test_extreme_magnitudes():
