@@ -174,8 +174,8 @@ def bench_segmented(es, W, torch, dev, steps, num_segments=65536, per_segment=Tr
     stream = torch.cuda.current_stream(dev)
     out_b = torch.empty(len(lengths), dtype=torch.float64, device=dev)
     out_e = torch.empty(len(lengths), dtype=torch.float64, device=dev)
-    warps, tile, tune_ms = es.exactsum_segmented_autotune(h, x.data_ptr(), d_off.data_ptr(), len(lengths),
-                                                          es.F64, out_b.data_ptr(), stream.cuda_stream)
+    warps, kind, tile, tune_ms = es.exactsum_segmented_autotune(h, x.data_ptr(), d_off.data_ptr(), len(lengths),
+                                                                es.F64, out_b.data_ptr(), stream.cuda_stream)
 
     def timed(fn, k):
         for _ in range(2):
@@ -203,7 +203,7 @@ def bench_segmented(es, W, torch, dev, steps, num_segments=65536, per_segment=Tr
          "speedup_vs_per_segment": round(each_ms / batched_ms, 2) if per_segment else None,
          "batched_gelem_s": round(total / batched_ms / 1e6, 2),
          "batched_hbm_gbs": round(total * 8 / batched_ms / 1e6, 1),
-         "tuned": {"warps": warps, "tile": tile, "ms": round(tune_ms, 3)},
+         "tuned": {"warps": warps, "reducer": ["register", "tma"][kind], "tile": tile, "ms": round(tune_ms, 3)},
          "bit_identical_to_per_segment": same}
     del x
     torch.cuda.empty_cache()
@@ -264,6 +264,49 @@ def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_st
             "engine": {"max_slots": max_slots, "budget_bytes": budget, "chunk_elems": chunk, "tile_elems": 1 << 15,
                        "max_steps_per_request": max_steps,
                        "steps": stats["steps"], "peak_resident": stats["peak_active"]}}
+
+
+def run_delta_sweep(args):
+    """Throughput of the FP64 exact sum over the paper's four dataset families
+    and exponent ranges delta (the design of the paper's Fig. 2 experiment,
+    on this GPU): the dense accumulator's cost should not depend on delta."""
+    import torch
+    import paper_1605_05436_gb300 as es
+    from paper_1605_05436_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    es.build()
+    n = 1 << args.log2n
+    h = es.handle_for(0)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream(dev)
+    rows = []
+    for family in (1, 2, 3, 4):
+        for delta in (10, 100, 500, 1000, 2000, 2046):
+            bits = W.family_f64(family, n, delta, seed=family)
+            x = torch.from_numpy(bits.view(np.int64)).to(dev)
+            for _ in range(3):
+                es.exactsum_sum(h, x.data_ptr(), n, es.F64, es.F64, es.RNE, out.data_ptr(), s.cuda_stream)
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            for _ in range(args.steps):
+                es.exactsum_sum(h, x.data_ptr(), n, es.F64, es.F64, es.RNE, out.data_ptr(), s.cuda_stream)
+            b.record(s)
+            torch.cuda.synchronize(dev)
+            ms = a.elapsed_time(b) / args.steps
+            rows.append({"family": family, "delta": delta, "ms": round(ms, 4),
+                         "gelem_s": round(n / ms / 1e6, 1), "gb_s": round(8 * n / ms / 1e6, 1)})
+            del x
+    peak, kind = measured_peaks()
+    line = {"metric": "exact-sum Gelem/s vs exponent range delta, four dataset families (FP64, 1xGB300)",
+            "unit": "Gelem/s", "n": n, "steps": args.steps, "higher_is_better": True, "data": "synthetic",
+            "families": {"1": "all positive", "2": "mixed signs", "3": "mixed signs minus the mean",
+                         "4": "exact sum zero (+/- pairs)"},
+            "peak_gb_s": peak, "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -435,6 +478,8 @@ def main():
                     help="segments of the batched measurement (65,536 is the benchmark workload)")
     ap.add_argument("--no-per-segment", action="store_true",
                     help="skip the one-launch-per-segment baseline (profiling runs)")
+    ap.add_argument("--delta-sweep", action="store_true",
+                    help="print the exponent-range sweep over the four dataset families instead")
     ap.add_argument("--requests", type=int, default=100_000,
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--log2n", type=int, default=LOG2N,
@@ -442,6 +487,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.delta_sweep:
+        return run_delta_sweep(args)
     return run_ours(args)
 
 

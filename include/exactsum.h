@@ -201,17 +201,20 @@ exactsum_status exactsum_sum_each(exactsum_t h, const void* d_x, const int64_t* 
                                   int64_t num_segments, int in_dtype, int out_dtype, int mode,
                                   void* d_results, exactsum_stream_t stream);
 
-/* Autotuner (synchronous): times each reducer configuration (two CTA
- * sizes x three tile sizes) on this very input, keeps the fastest for the
- * input format and size class, and reports it through the non-NULL output
- * pointers.  d_results_scratch: num_segments elements of in_dtype. */
+/* Autotuner (synchronous): times each reducer configuration on this very
+ * input -- the register-streaming reducer with two CTA sizes and the
+ * TMA-ring reducer (kind 1), each with three tile sizes -- keeps the
+ * fastest for the input format and size class, and reports it through the
+ * non-NULL output pointers (kind: 0 register streaming, 1 TMA ring).
+ * d_results_scratch: num_segments elements of in_dtype. */
 exactsum_status exactsum_segmented_autotune(exactsum_t h, const void* d_x, const int64_t* d_offsets,
                                             int64_t num_segments, int in_dtype,
                                             void* d_results_scratch, exactsum_stream_t stream,
-                                            int* best_warps, int64_t* best_tile, float* best_ms);
+                                            int* best_warps, int* best_kind, int64_t* best_tile,
+                                            float* best_ms);
 
 /* Save / load the autotuner's table as JSON
- * ({"segmented": [{"in_dtype", "log2_segments", "warps", "tile", "ms"}...]}). */
+ * ({"segmented": [{"in_dtype", "log2_segments", "warps", "kind", "tile", "ms"}...]}). */
 exactsum_status exactsum_tuning_save(exactsum_t h, const char* path);
 exactsum_status exactsum_tuning_load(exactsum_t h, const char* path);
 

@@ -48,7 +48,7 @@ _SIGNATURES = {
     "exactsum_segmented_sum": [_vp, _vp, _vp, _i64, _int, _int, _int, _vp, _vp],
     "exactsum_sum_each": [_vp, _vp, _vp, _i64, _int, _int, _int, _vp, _vp],
     "exactsum_segmented_autotune": [_vp, _vp, _vp, _i64, _int, _vp, _vp, ctypes.POINTER(_int),
-                                    ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_float)],
+                                    ctypes.POINTER(_int), ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_float)],
     "exactsum_tuning_save": [_vp, ctypes.c_char_p],
     "exactsum_tuning_load": [_vp, ctypes.c_char_p],
     "exactsum_device_status": [_vp, ctypes.POINTER(_i64)],
@@ -171,12 +171,13 @@ def exactsum_sum_each(handle, d_x, h_offsets, num_segments, in_dtype, out_dtype,
 
 def exactsum_segmented_autotune(handle, d_x, d_offsets, num_segments, in_dtype, d_results_scratch,
                                 stream):
-    """Returns (warps, tile, ms) of the fastest reducer configuration."""
-    w, t, ms = _int(0), _i64(0), ctypes.c_float(0)
+    """Returns (warps, kind, tile, ms) of the fastest reducer configuration
+    (kind 0: register streaming, 1: TMA ring)."""
+    w, k, t, ms = _int(0), _int(0), _i64(0), ctypes.c_float(0)
     _check(library().exactsum_segmented_autotune(handle, d_x, d_offsets, num_segments, in_dtype,
-                                                 d_results_scratch, stream, ctypes.byref(w),
+                                                 d_results_scratch, stream, ctypes.byref(w), ctypes.byref(k),
                                                  ctypes.byref(t), ctypes.byref(ms)), handle)
-    return w.value, t.value, ms.value
+    return w.value, k.value, t.value, ms.value
 
 
 def exactsum_tuning_save(handle, path: str) -> None:

@@ -13,6 +13,7 @@
 // A reducer configuration of the segmented kernel.
 struct es_seg_config {
   int warps = 8;        // warps per CTA
+  int kind = 0;         // reducer form: 0 register streaming, 1 TMA ring
   int64_t tile = 0;     // elements per tile
   float ms = -1.0f;     // measured time per call (autotuner), -1 if unmeasured
 };
@@ -25,6 +26,7 @@ struct es_graph_key {
   int in, out, mode;
   void* results;
   int warps;
+  int kind;
   int64_t tile;
 };
 

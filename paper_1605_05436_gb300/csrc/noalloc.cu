@@ -151,7 +151,7 @@ extern "C" exactsum_status exactsum_segmented_sum_noalloc(const void* d_x, const
   a.seg_acc = (int64_t*)(ds.base + OFF_ACC);
   a.counters = (unsigned long long*)(ds.base + OFF_COUNTERS);
   a.status = (unsigned long long*)(ds.base + OFF_STATUS);
-  e = es::seg_enqueue(in_dtype, a, es::seg_warps_choice(in_dtype, 0), ds.num_sms, s);
+  e = es::seg_enqueue(in_dtype, a, es::seg_warps_choice(in_dtype, 0), es::SEG_KIND_REGISTER, ds.num_sms, s);
   if (e != cudaSuccess) {
     char msg[160];
     std::snprintf(msg, sizeof msg, "segmented launch: %s", cudaGetErrorString(e));

@@ -133,11 +133,21 @@ exactsum_status run_segmented(exactsum_t h, const void* x, const int64_t* off, i
   if (st != EXACTSUM_OK) return st;
   es::SegArgs a = make_args(h, x, off, S, out, mode, results, cfg.tile);
   if (capturing || !use_graph) {
-    e = es::seg_enqueue(in, a, cfg.warps, h->num_sms, stream);
+    e = es::seg_enqueue(in, a, cfg.warps, cfg.kind, h->num_sms, stream);
     if (e != cudaSuccess) return es_cuda_fail(h, e, "segmented launch");
     return EXACTSUM_OK;
   }
-  es_graph_key key{x, off, S, in, out, mode, results, cfg.warps, cfg.tile};
+  es_graph_key key{};  // value-initialised: padding bytes compare equal
+  key.x = x;
+  key.off = off;
+  key.S = S;
+  key.in = in;
+  key.out = out;
+  key.mode = mode;
+  key.results = results;
+  key.warps = cfg.warps;
+  key.kind = cfg.kind;
+  key.tile = cfg.tile;
   cudaGraphExec_t exec = nullptr;
   for (size_t i = 0; i < h->seg_graphs.size(); ++i) {
     if (std::memcmp(&h->seg_graphs[i].key, &key, sizeof key) == 0) {
@@ -153,7 +163,7 @@ exactsum_status run_segmented(exactsum_t h, const void* x, const int64_t* off, i
     }
     if ((e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return es_cuda_fail(h, e, "cudaStreamBeginCapture");
-    cudaError_t le = es::seg_enqueue(in, a, cfg.warps, h->num_sms, h->capture_stream);
+    cudaError_t le = es::seg_enqueue(in, a, cfg.warps, cfg.kind, h->num_sms, h->capture_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(h->capture_stream, &graph);
     if (le != cudaSuccess) {
@@ -202,8 +212,8 @@ exactsum_status exactsum_segmented_sum(exactsum_t h, const void* d_x, const int6
 
 exactsum_status exactsum_segmented_autotune(exactsum_t h, const void* d_x, const int64_t* d_offsets,
                                             int64_t num_segments, int in_dtype, void* d_results_scratch,
-                                            exactsum_stream_t stream, int* best_warps, int64_t* best_tile,
-                                            float* best_ms) {
+                                            exactsum_stream_t stream, int* best_warps, int* best_kind,
+                                            int64_t* best_tile, float* best_ms) {
   exactsum_status st =
       check_seg_args(h, d_x, d_offsets, num_segments, in_dtype, in_dtype, EXACTSUM_RNE, d_results_scratch);
   if (st != EXACTSUM_OK) return st;
@@ -217,10 +227,13 @@ exactsum_status exactsum_segmented_autotune(exactsum_t h, const void* d_x, const
   es_seg_config best{};
   best.ms = -1.0f;
   const int64_t tiles_bytes[] = {64 << 10, 256 << 10, 1 << 20};
-  for (int wi = 0; wi < 2; ++wi) {
+  // candidates: register form with either CTA size, and the TMA form
+  const int forms[3][2] = {{0, es::SEG_KIND_REGISTER}, {1, es::SEG_KIND_REGISTER}, {2, es::SEG_KIND_TMA}};
+  for (const auto& form : forms) {
     for (int64_t tb : tiles_bytes) {
       es_seg_config c;
-      c.warps = es::seg_warps_choice(in_dtype, wi);
+      c.warps = es::seg_warps_choice(in_dtype, form[0]);
+      c.kind = form[1];
       c.tile = tb / elem_bytes(in_dtype);
       c.ms = 0;
       // warm once, then time three calls
@@ -249,6 +262,7 @@ exactsum_status exactsum_segmented_autotune(exactsum_t h, const void* d_x, const
   if (st != EXACTSUM_OK) return st;
   h->seg_tuning[in_dtype * 64 + ceil_log2(num_segments)] = best;
   if (best_warps) *best_warps = best.warps;
+  if (best_kind) *best_kind = best.kind;
   if (best_tile) *best_tile = best.tile;
   if (best_ms) *best_ms = best.ms;
   return EXACTSUM_OK;
@@ -262,7 +276,8 @@ exactsum_status exactsum_tuning_save(exactsum_t h, const char* path) {
   bool first = true;
   for (const auto& kv : h->seg_tuning) {
     f << (first ? "" : ", ") << "{\"in_dtype\": " << kv.first / 64 << ", \"log2_segments\": " << kv.first % 64
-      << ", \"warps\": " << kv.second.warps << ", \"tile\": " << kv.second.tile << ", \"ms\": " << kv.second.ms
+      << ", \"warps\": " << kv.second.warps << ", \"kind\": " << kv.second.kind << ", \"tile\": "
+      << kv.second.tile << ", \"ms\": " << kv.second.ms
       << "}";
     first = false;
   }
@@ -292,13 +307,19 @@ exactsum_status exactsum_tuning_load(exactsum_t h, const char* path) {
       v = std::atoll(obj.c_str() + c + 1);
       return true;
     };
-    long long in = 0, lg = 0, w = 0, tile = 0;
+    long long in = 0, lg = 0, w = 0, tile = 0, kind = 0;
     if (field("in_dtype", in) && field("log2_segments", lg) && field("warps", w) && field("tile", tile)) {
-      if (in < 0 || in > 2 || lg < 0 || lg > 62 || tile <= 0 ||
-          (w != es::seg_warps_choice((int)in, 0) && w != es::seg_warps_choice((int)in, 1)))
+      field("kind", kind);  // absent in older files: register form
+      const bool shape_ok =
+          kind == es::SEG_KIND_TMA
+              ? (in >= 0 && in <= 2 && w == es::seg_warps_choice((int)in, 2))
+              : (kind == es::SEG_KIND_REGISTER && in >= 0 && in <= 2 &&
+                 (w == es::seg_warps_choice((int)in, 0) || w == es::seg_warps_choice((int)in, 1)));
+      if (in < 0 || in > 2 || lg < 0 || lg > 62 || tile <= 0 || !shape_ok)
         return fail(h, EXACTSUM_EINVAL, "invalid tuning entry");
       es_seg_config c;
       c.warps = (int)w;
+      c.kind = (int)kind;
       c.tile = tile;
       c.ms = -1.0f;
       h->seg_tuning[(int)in * 64 + (int)lg] = c;

@@ -35,6 +35,7 @@
 #include "handle.h"
 #include "segmented.h"
 #include "stream.cuh"
+#include "tma.cuh"
 
 namespace es {
 
@@ -137,6 +138,79 @@ __global__ void __launch_bounds__(PLAN_T) seg_base_kernel(SegArgs a) {
   }
 }
 
+// Per-tile work item of the reducers.
+struct TileWork {
+  int64_t s;       // segment
+  int64_t ntiles;  // tiles of the segment
+  int64_t lo, hi;  // element range of this tile
+};
+
+__device__ __forceinline__ TileWork tile_work(const SegArgs& a, int64_t tile) {
+  TileWork w;
+  w.s = a.tile_seg[tile];
+  const int64_t tb = a.tile_base[w.s];
+  w.ntiles = a.tile_base[w.s + 1] - tb;
+  w.lo = a.off[w.s] + (tile - tb) * a.tile;
+  w.hi = min(a.off[w.s + 1], w.lo + a.tile);
+  return w;
+}
+
+// After a tile has been added into the warp's columns: regularise, classify,
+// merge the warp carry-free, clear the columns, and either round the segment
+// (a one-tile segment) or add the partial into the segment's accumulator;
+// the warp that retires the last tile rounds it and clears the accumulator.
+template <int DT, int T, int W>
+__device__ __forceinline__ void seg_finish_tile(const SegArgs& a, const TileWork& w, const RangeSplit& r,
+                                                int64_t* digits, int64_t* col, int64_t (*wacc)[ACC_WORDS],
+                                                uint32_t (*wlimbs)[ACC_DIGITS], uint32_t emax) {
+  constexpr int ND = Geometry<DT>::DIGITS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  regularise<DT, T>(col);
+  uint32_t flags = 24u;
+  if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) flags = rescan_split<DT, 32>(a.x, r, lane);
+  flags = __reduce_or_sync(0xffffffffu, flags);
+  __syncwarp();
+
+  // ---- warp merge (carry-free), then clear the columns ----
+  int64_t d0, d1, d2;
+  warp_merge<DT, T>(digits + warp * 32, lane, d0, d1, d2);
+  __syncwarp();
+  for (int i = 0; i < ND; ++i) col[i * T] = 0;
+  if (lane + 64 >= ACC_DIGITS) d2 = (lane + 64 < ACC_WORDS) ? flag_word(lane + 64, flags, w.hi - w.lo) : 0;
+
+  if (w.ntiles == 1) {
+    wacc[warp][lane] = d0;
+    wacc[warp][lane + 32] = d1;
+    if (lane + 64 < ACC_WORDS) wacc[warp][lane + 64] = d2;
+    __syncwarp();
+    if (lane == 0) store_indexed(a.results, a.out, w.s, finalize_acc(wacc[warp], wlimbs[warp], DT, a.out, a.mode));
+    __syncwarp();
+  } else {
+    unsigned long long* acc = (unsigned long long*)(a.seg_acc + w.s * ACC_WORDS);
+    if (d0) atomicAdd(acc + lane, (unsigned long long)d0);
+    if (d1) atomicAdd(acc + lane + 32, (unsigned long long)d1);
+    if (lane + 64 < ACC_WORDS && d2) atomicAdd(acc + lane + 64, (unsigned long long)d2);
+    __threadfence();
+    __syncwarp();
+    unsigned last = 0;
+    if (lane == 0) last = (atomicSub(&a.remaining[w.s], 1u) == 1u) ? 1u : 0u;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence();
+      wacc[warp][lane] = (int64_t)__ldcg(acc + lane);
+      wacc[warp][lane + 32] = (int64_t)__ldcg(acc + lane + 32);
+      if (lane + 64 < ACC_WORDS) wacc[warp][lane + 64] = (int64_t)__ldcg(acc + lane + 64);
+      acc[lane] = 0;
+      acc[lane + 32] = 0;
+      if (lane + 64 < ACC_WORDS) acc[lane + 64] = 0;
+      __syncwarp();
+      if (lane == 0) store_indexed(a.results, a.out, w.s, finalize_acc(wacc[warp], wlimbs[warp], DT, a.out, a.mode));
+      __syncwarp();
+    }
+  }
+}
+
+// Register-streaming reducer: each lane loads its own vectors.
 template <int DT, int W, int U>
 __global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel(SegArgs a) {
   constexpr int T = W * 32;
@@ -146,7 +220,7 @@ __global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel(SegArgs a) {
   __shared__ int64_t wacc[W][ACC_WORDS];
   __shared__ uint32_t wlimbs[W][ACC_DIGITS];
 
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int t = threadIdx.x, lane = t & 31;
   int64_t* col = digits + t;
   for (int i = 0; i < ND; ++i) col[i * T] = 0;
   const int64_t total = (int64_t)__ldcg((const unsigned long long*)&a.counters[CNT_TOTAL]);
@@ -157,61 +231,118 @@ __global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel(SegArgs a) {
     if (lane == 0) tk = atomicAdd(&a.counters[CNT_QUEUE], 1ull);
     const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, tk, 0);
     if (tile >= total) break;
-    const int64_t s = a.tile_seg[tile];
-    const int64_t tb = a.tile_base[s];
-    const int64_t ntiles = a.tile_base[s + 1] - tb;
-    const int64_t seg_lo = a.off[s], seg_hi = a.off[s + 1];
-    const int64_t lo = seg_lo + (tile - tb) * a.tile;
-    const int64_t hi = min(seg_hi, lo + a.tile);
-
-    // ---- accumulate this tile (warp-cooperative, lane-private columns) ----
-    const RangeSplit r = split_range<DT>(a.x, lo, hi);
+    const TileWork w = tile_work(a, tile);
+    const RangeSplit r = split_range<DT>(a.x, w.lo, w.hi);
     uint32_t emax = 0;
     int reg_left = REG_EVERY;
     add_split<DT, T, 32, U>(col, a.x, r, lane, emax, reg_left);
-    regularise<DT, T>(col);
-    uint32_t flags = 24u;
-    if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) flags = rescan_split<DT, 32>(a.x, r, lane);
-    flags = __reduce_or_sync(0xffffffffu, flags);
-    __syncwarp();
+    seg_finish_tile<DT, T, W>(a, w, r, digits, col, wacc, wlimbs, emax);
+  }
+}
 
-    // ---- warp merge (carry-free), then clear the columns ----
-    int64_t d0, d1, d2;
-    warp_merge<DT, T>(digits + warp * 32, lane, d0, d1, d2);
-    __syncwarp();
-    for (int i = 0; i < ND; ++i) col[i * T] = 0;
-    if (lane + 64 >= ACC_DIGITS) d2 = (lane + 64 < ACC_WORDS) ? flag_word(lane + 64, flags, hi - lo) : 0;
+// TMA reducer: each warp streams its own tile through an S-stage ring in
+// shared memory; lane 0 issues the bulk copies (cp.async.bulk) S batches
+// ahead and refills a stage as soon as the warp has copied it to registers.
+// Every wait is bounded; a timeout sets STATUS_TIMEOUT, waits (bounded) for
+// the warp's copies still in flight and retires the warp.
+template <int DT, int W, int U, int S>
+__global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel_tma(SegArgs a) {
+  constexpr int T = W * 32;
+  constexpr int ND = Geometry<DT>::DIGITS;
+  constexpr int EB = Geometry<DT>::ELEM_BYTES;
+  constexpr int EPV = 16 / EB;
+  constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
+  constexpr int B = 32 * U;  // vectors per batch of one warp
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  int64_t* digits = reinterpret_cast<int64_t*>(smem_raw);                      // ND x T
+  uint4* rings = reinterpret_cast<uint4*>(smem_raw + (size_t)ND * T * 8);      // W x S x B
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rings + (size_t)W * S * B);     // W x S
+  __shared__ int64_t wacc[W][ACC_WORDS];
+  __shared__ uint32_t wlimbs[W][ACC_DIGITS];
 
-    if (ntiles == 1) {
-      wacc[warp][lane] = d0;
-      wacc[warp][lane + 32] = d1;
-      if (lane + 64 < ACC_WORDS) wacc[warp][lane + 64] = d2;
-      __syncwarp();
-      if (lane == 0) store_indexed(a.results, a.out, s, finalize_acc(wacc[warp], wlimbs[warp], DT, a.out, a.mode));
-      __syncwarp();
-    } else {
-      unsigned long long* acc = (unsigned long long*)(a.seg_acc + s * ACC_WORDS);
-      if (d0) atomicAdd(acc + lane, (unsigned long long)d0);
-      if (d1) atomicAdd(acc + lane + 32, (unsigned long long)d1);
-      if (lane + 64 < ACC_WORDS && d2) atomicAdd(acc + lane + 64, (unsigned long long)d2);
-      __threadfence();
-      __syncwarp();
-      unsigned last = 0;
-      if (lane == 0) last = (atomicSub(&a.remaining[s], 1u) == 1u) ? 1u : 0u;
-      last = __shfl_sync(0xffffffffu, last, 0);
-      if (last) {
-        __threadfence();
-        wacc[warp][lane] = (int64_t)__ldcg(acc + lane);
-        wacc[warp][lane + 32] = (int64_t)__ldcg(acc + lane + 32);
-        if (lane + 64 < ACC_WORDS) wacc[warp][lane + 64] = (int64_t)__ldcg(acc + lane + 64);
-        acc[lane] = 0;
-        acc[lane + 32] = 0;
-        if (lane + 64 < ACC_WORDS) acc[lane + 64] = 0;
-        __syncwarp();
-        if (lane == 0) store_indexed(a.results, a.out, s, finalize_acc(wacc[warp], wlimbs[warp], DT, a.out, a.mode));
-        __syncwarp();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  int64_t* col = digits + t;
+  for (int i = 0; i < ND; ++i) col[i * T] = 0;
+  uint4* ring = rings + (size_t)warp * S * B;
+  uint64_t* full = bars + warp * S;
+  if (lane == 0) {
+    for (int k = 0; k < S; ++k) mbar_init(&full[k], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  const int64_t total = (int64_t)__ldcg((const unsigned long long*)&a.counters[CNT_TOTAL]);
+  if (total > a.map_capacity) return;  // flagged by the planner; results are NaN
+
+  uint32_t g = 0;  // batches this warp has consumed: stage g % S, phase parity (g / S) & 1
+  for (;;) {
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(&a.counters[CNT_QUEUE], 1ull);
+    const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, tk, 0);
+    if (tile >= total) break;
+    const TileWork w = tile_work(a, tile);
+    const RangeSplit r = split_range<DT>(a.x, w.lo, w.hi);
+    uint32_t emax = 0;
+    int reg_left = REG_EVERY;
+    if (lane < r.head_n) add_one<DT, T>(col, load_one<DT>(a.x, r.vlo - r.head_n + lane), emax);
+    const uint4* vp = reinterpret_cast<const uint4*>((const char*)a.x + r.vlo * EB);
+    const int64_t nb = (r.nvec + B - 1) / B;
+    if (lane == 0) {
+      for (int64_t k = 0; k < nb && k < S; ++k) {
+        const uint32_t st = (g + (uint32_t)k) % S;
+        const int64_t nv = min((int64_t)B, r.nvec - k * B);
+        mbar_arrive_expect_tx(&full[st], (uint32_t)(nv * 16));
+        bulk_copy_g2s(ring + (size_t)st * B, vp + k * B, (uint32_t)(nv * 16), &full[st]);
       }
     }
+    bool ok = true;
+    int64_t k = 0;
+    for (; k < nb; ++k) {
+      const uint32_t gk = g + (uint32_t)k;
+      const uint32_t st = gk % S;
+      ok = mbar_wait(&full[st], (gk / S) & 1u);
+      if (__any_sync(0xffffffffu, !ok)) {
+        ok = false;
+        break;
+      }
+      const int64_t nv = min((int64_t)B, r.nvec - k * B);
+      const uint4* stage = ring + (size_t)st * B;
+      uint4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (lane + 32 * u < nv) v[u] = lds128(stage + lane + 32 * u);
+      __syncwarp();
+      if (lane == 0 && k + S < nb) {
+        // the warp's reads of this stage are done: order them before the
+        // asynchronous refill of the same stage
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const int64_t nv2 = min((int64_t)B, r.nvec - (k + S) * B);
+        mbar_arrive_expect_tx(&full[st], (uint32_t)(nv2 * 16));
+        bulk_copy_g2s(ring + (size_t)st * B, vp + (k + S) * B, (uint32_t)(nv2 * 16), &full[st]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (lane + 32 * u < nv) add_vec<DT, T>(col, v[u], emax);
+      reg_left -= U * EPV;
+      if (reg_left <= 0) {
+        regularise<DT, T>(col);
+        reg_left = REG_EVERY;
+      }
+    }
+    if (!ok) {
+      // copies for batches k .. min(k + S, nb) - 1 may still be in flight
+      if (lane == 0) {
+        for (int64_t j = k; j < nb && j < k + S; ++j) {
+          const uint32_t gj = g + (uint32_t)j;
+          mbar_wait(&full[gj % S], (gj / S) & 1u);
+        }
+        atomicOr(a.status, STATUS_TIMEOUT);
+      }
+      __syncwarp();
+      return;
+    }
+    g += (uint32_t)nb;
+    if (lane < r.tail_n) add_one<DT, T>(col, load_one<DT>(a.x, r.tail_lo + lane), emax);
+    seg_finish_tile<DT, T, W>(a, w, r, digits, col, wacc, wlimbs, emax);
   }
 }
 
@@ -226,11 +357,46 @@ static cudaError_t set_attr_t() {
                               (int)SMEM);
 }
 
+// TMA reducer shapes: 2 stages of 8 vectors per lane; 8 warps for FP64
+// (66-digit columns), 12 for FP32/BF16 (33-digit columns).
+#ifndef ES_SEGTMA_F64_U
+#define ES_SEGTMA_F64_U 10
+#endif
+#ifndef ES_SEGTMA_F64_S
+#define ES_SEGTMA_F64_S 2
+#endif
+template <int DT> struct SegTma;
+template <> struct SegTma<F64> { static constexpr int W = 8, U = ES_SEGTMA_F64_U, S = ES_SEGTMA_F64_S; };
+template <> struct SegTma<F32> { static constexpr int W = 12, U = 8, S = 2; };
+template <> struct SegTma<BF16> { static constexpr int W = 12, U = 8, S = 2; };
+
+template <int DT>
+constexpr size_t seg_tma_smem() {
+  using C = SegTma<DT>;
+  return (size_t)Geometry<DT>::DIGITS * C::W * 32 * 8 + (size_t)C::W * C::S * 32 * C::U * 16 +
+         (size_t)C::W * C::S * 8;
+}
+
+template <int DT>
+static cudaError_t set_attr_tma_t() {
+  using C = SegTma<DT>;
+  static_assert(seg_tma_smem<DT>() + (size_t)C::W * (ACC_WORDS * 8 + ACC_DIGITS * 4) <= 232448,
+                "shared memory per CTA");
+  return cudaFuncSetAttribute(seg_sum_kernel_tma<DT, C::W, C::U, C::S>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_tma_smem<DT>());
+}
+
 template <int DT, int W>
 static void launch_main_direct(const SegArgs& a, int grid, cudaStream_t st) {
   constexpr int U = 4;
   constexpr size_t SMEM = (size_t)Geometry<DT>::DIGITS * W * 32 * sizeof(int64_t);
   seg_sum_kernel<DT, W, U><<<grid, W * 32, SMEM, st>>>(a);
+}
+
+template <int DT>
+static void launch_main_tma(const SegArgs& a, int grid, cudaStream_t st) {
+  using C = SegTma<DT>;
+  seg_sum_kernel_tma<DT, C::W, C::U, C::S><<<grid, C::W * 32, seg_tma_smem<DT>(), st>>>(a);
 }
 
 static cudaError_t configure_kernels(int dev) {
@@ -243,16 +409,20 @@ static cudaError_t configure_kernels(int dev) {
   if ((e = set_attr_t<F32, 16>()) != cudaSuccess) return e;
   if ((e = set_attr_t<BF16, 8>()) != cudaSuccess) return e;
   if ((e = set_attr_t<BF16, 16>()) != cudaSuccess) return e;
+  if ((e = set_attr_tma_t<F64>()) != cudaSuccess) return e;
+  if ((e = set_attr_tma_t<F32>()) != cudaSuccess) return e;
+  if ((e = set_attr_tma_t<BF16>()) != cudaSuccess) return e;
   if (dev >= 0 && dev < 64) done[dev] = true;
   return cudaSuccess;
 }
 
 int seg_warps_choice(int in_dt, int idx) {
+  if (idx == 2) return in_dt == F64 ? SegTma<F64>::W : SegTma<F32>::W;
   if (in_dt == F64) return idx == 0 ? 8 : 12;
   return idx == 0 ? 8 : 16;
 }
 
-cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int num_sms, cudaStream_t st) {
+cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int kind, int num_sms, cudaStream_t st) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -262,6 +432,14 @@ cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int num_sms, cud
   seg_scan_kernel<<<1, PLAN_T, 0, st>>>(a, nblocks);
   seg_base_kernel<<<(unsigned)nblocks, PLAN_T, 0, st>>>(a);
   const int grid = num_sms;
+  if (kind == SEG_KIND_TMA) {
+    switch (in_dt) {
+      case F64: launch_main_tma<F64>(a, grid, st); break;
+      case F32: launch_main_tma<F32>(a, grid, st); break;
+      default: launch_main_tma<BF16>(a, grid, st); break;
+    }
+    return cudaGetLastError();
+  }
   switch (in_dt) {
     case F64:
       if (warps == 12) launch_main_direct<F64, 12>(a, grid, st);

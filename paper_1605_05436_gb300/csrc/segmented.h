@@ -27,9 +27,13 @@ struct SegArgs {
   unsigned long long* status;    // device status word (STATUS_* bits)
 };
 
+// Reducer forms: register streaming (warps choice 0 or 1) or the TMA ring.
+enum : int { SEG_KIND_REGISTER = 0, SEG_KIND_TMA = 1 };
+
 // Enqueue the four kernels of one segmented sum on `st`.
-cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int num_sms, cudaStream_t st);
-// Warps per CTA of the reducer kernel for a dtype: choice 0 or 1.
+cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int kind, int num_sms, cudaStream_t st);
+// Warps per CTA of the reducer for a dtype: register form choice 0 or 1;
+// choice 2 is the TMA form's fixed shape.
 int seg_warps_choice(int in_dt, int idx);
 
 }  // namespace es

@@ -91,6 +91,47 @@ def cancelling_residue(n: int, seed: int = 0, residue: int = 1024,
     return rng.uniform(-1.0, 1.0, residue).view(np.uint64)
 
 
+def family_f64(family: int, n: int, delta: int, seed: int = 0) -> np.ndarray:
+    """One of the four dataset families of the paper's experiments (Section
+    6.3), with exponents spread over a range of width ``delta`` (centred on
+    0, at most 2046 wide):
+
+    1. all positive (condition number 1);
+    2. mixed signs, uniform random;
+    3. Anderson's ill-conditioned data: mixed signs, minus the float mean;
+    4. exact sum zero: random values and their exact negations, shuffled.
+
+    Values are random-sign (positive for family 1) doubles with unbiased
+    exponent uniform in [-delta/2, delta/2] and a uniform 52-bit fraction.
+    """
+    if not 1 <= family <= 4:
+        raise ValueError("family is 1..4")
+    delta = max(0, min(int(delta), 2046))
+    emin, emax = -(delta // 2), delta - delta // 2
+    emin, emax = max(emin, -1022), min(emax, 1023)
+    rng = np.random.default_rng(seed)
+    if family == 4:
+        half = n // 2
+        out = np.empty(n, dtype=np.uint64)
+        out[:half] = _random_f64_bits(rng, half, emin, emax)
+        out[half:2 * half] = out[:half] ^ np.uint64(1 << 63)
+        if n % 2:
+            out[-1] = 0
+        rng.shuffle(out)
+        return out
+    bits = _random_f64_bits(rng, n, emin, emax)
+    if family == 1:
+        bits &= np.uint64((1 << 63) - 1)
+    if family == 3:
+        x = bits.view(np.float64)
+        with np.errstate(over="ignore", invalid="ignore"):
+            mean = x.mean()
+        if np.isfinite(mean):
+            x = x - mean
+        bits = x.view(np.uint64)
+    return bits
+
+
 def wide_f32(n: int, seed: int = 0, subnormal_frac: float = 0.01) -> np.ndarray:
     """FP32 bits: random sign; with probability 1 - subnormal_frac a normal with
     biased exponent uniform in [1, 254] and uniform 23-bit fraction, else a

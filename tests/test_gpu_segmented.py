@@ -145,13 +145,13 @@ def test_autotune_and_tuning_file(tmp_path):
     scratch = torch.empty(len(lengths), dtype=torch.float64, device=DEV)
     h = es.handle_for(0)
     s = torch.cuda.current_stream().cuda_stream
-    warps, tile, ms = es.exactsum_segmented_autotune(h, x.data_ptr(), d_off.data_ptr(), len(lengths), es.F64,
-                                                     scratch.data_ptr(), s)
-    assert warps in (8, 12) and tile > 0 and ms > 0
+    warps, kind, tile, ms = es.exactsum_segmented_autotune(h, x.data_ptr(), d_off.data_ptr(), len(lengths),
+                                                           es.F64, scratch.data_ptr(), s)
+    assert warps in (8, 12) and kind in (0, 1) and tile > 0 and ms > 0
     p = str(tmp_path / "tuning.json")
     es.exactsum_tuning_save(h, p)
     text = open(p).read()
-    assert '"warps": %d' % warps in text and '"tile": %d' % tile in text
+    assert '"warps": %d' % warps in text and '"tile": %d' % tile in text and '"kind": %d' % kind in text
     es.exactsum_tuning_load(h, p)
     got = es.segmented_sum(x, d_off)
     torch.cuda.synchronize()
@@ -195,3 +195,31 @@ def test_anderson_full_sampled(anderson_full):
     for s in sorted(sample):
         seg = x[int(off[s]):int(off[s + 1])].cpu().numpy().view(np.uint64)
         assert int(got_bits[s]) == oracle.exact_sum(seg, threads=16), s
+
+
+@pytest.mark.parametrize("dt", [es.F64, es.F32, es.BF16])
+def test_tma_reducer_forced(tmp_path, dt):
+    """The TMA-ring reducer (chosen through a tuning file) gives the oracle's
+    bits on edge lengths and on random segments, with small and large tiles."""
+    h = es.handle_for(0)
+    lengths = np.array(EDGE_LENGTHS * 3, dtype=np.int64)
+    off = W.csr_offsets(lengths) + 1
+    bits = make_bits(dt, int(off[-1]) + 3, 40 + dt)
+    S = len(lengths)
+    lg = int(np.ceil(np.log2(S)))
+    warps = 8 if dt == es.F64 else 12
+    for tile in (4096, 65536):
+        p = tmp_path / f"tma_{dt}_{tile}.json"
+        p.write_text('{"segmented": [{"in_dtype": %d, "log2_segments": %d, "warps": %d, "kind": 1, '
+                     '"tile": %d, "ms": -1}]}' % (dt, lg, warps, tile))
+        es.exactsum_tuning_load(h, str(p))
+        for o, m in ((dt, es.RNE), (es.F64, es.RUP)):
+            got = run_segmented(bits, off, dt, o, m)
+            want = oracle.exact_sum_segmented(bits, off, dt, o, m, threads=8)
+            assert np.array_equal(got, want.astype(np.uint64)), (tile, o, m)
+    # restore the default choice for this size class
+    p = tmp_path / "reg.json"
+    p.write_text('{"segmented": [{"in_dtype": %d, "log2_segments": %d, "warps": 8, "kind": 0, "tile": %d}]}'
+                 % (dt, lg, (256 << 10) // es.ITEMSIZE[dt]))
+    es.exactsum_tuning_load(h, str(p))
+    assert es.exactsum_device_status(h) & 4 == 0  # no wait timed out
