@@ -203,7 +203,7 @@ def bench_segmented(es, W, torch, dev, steps, num_segments=65536, per_segment=Tr
          "speedup_vs_per_segment": round(each_ms / batched_ms, 2) if per_segment else None,
          "batched_gelem_s": round(total / batched_ms / 1e6, 2),
          "batched_hbm_gbs": round(total * 8 / batched_ms / 1e6, 1),
-         "tuned": {"warps": warps, "reducer": ["register", "tma"][kind], "tile": tile, "ms": round(tune_ms, 3)},
+         "tuned": {"warps": warps, "reducer": ["register", "tma", "window"][kind], "tile": tile, "ms": round(tune_ms, 3)},
          "bit_identical_to_per_segment": same}
     del x
     torch.cuda.empty_cache()

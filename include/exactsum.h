@@ -202,10 +202,13 @@ exactsum_status exactsum_sum_each(exactsum_t h, const void* d_x, const int64_t* 
                                   void* d_results, exactsum_stream_t stream);
 
 /* Autotuner (synchronous): times each reducer configuration on this very
- * input -- the register-streaming reducer with two CTA sizes and the
- * TMA-ring reducer (kind 1), each with three tile sizes -- keeps the
- * fastest for the input format and size class, and reports it through the
- * non-NULL output pointers (kind: 0 register streaming, 1 TMA ring).
+ * input -- the register-streaming reducer with two CTA sizes, the
+ * TMA-ring reducer (kind 1) and the windowed reducer (kind 2: narrow
+ * per-lane digit windows plus an exact overflow accumulator, fast when a
+ * tile's exponents are concentrated), each with three tile sizes -- keeps
+ * the fastest for the input format and size class, and reports it through
+ * the non-NULL output pointers (kind: 0 register streaming, 1 TMA ring,
+ * 2 windowed).
  * d_results_scratch: num_segments elements of in_dtype. */
 exactsum_status exactsum_segmented_autotune(exactsum_t h, const void* d_x, const int64_t* d_offsets,
                                             int64_t num_segments, int in_dtype,

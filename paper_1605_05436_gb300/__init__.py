@@ -172,7 +172,7 @@ def exactsum_sum_each(handle, d_x, h_offsets, num_segments, in_dtype, out_dtype,
 def exactsum_segmented_autotune(handle, d_x, d_offsets, num_segments, in_dtype, d_results_scratch,
                                 stream):
     """Returns (warps, kind, tile, ms) of the fastest reducer configuration
-    (kind 0: register streaming, 1: TMA ring)."""
+    (kind 0: register streaming, 1: TMA ring, 2: windowed)."""
     w, k, t, ms = _int(0), _int(0), _i64(0), ctypes.c_float(0)
     _check(library().exactsum_segmented_autotune(handle, d_x, d_offsets, num_segments, in_dtype,
                                                  d_results_scratch, stream, ctypes.byref(w), ctypes.byref(k),

@@ -228,7 +228,8 @@ exactsum_status exactsum_segmented_autotune(exactsum_t h, const void* d_x, const
   best.ms = -1.0f;
   const int64_t tiles_bytes[] = {64 << 10, 256 << 10, 1 << 20};
   // candidates: register form with either CTA size, and the TMA form
-  const int forms[3][2] = {{0, es::SEG_KIND_REGISTER}, {1, es::SEG_KIND_REGISTER}, {2, es::SEG_KIND_TMA}};
+  const int forms[4][2] = {{0, es::SEG_KIND_REGISTER}, {1, es::SEG_KIND_REGISTER}, {2, es::SEG_KIND_TMA},
+                           {3, es::SEG_KIND_WINDOW}};
   for (const auto& form : forms) {
     for (int64_t tb : tiles_bytes) {
       es_seg_config c;
@@ -310,11 +311,13 @@ exactsum_status exactsum_tuning_load(exactsum_t h, const char* path) {
     long long in = 0, lg = 0, w = 0, tile = 0, kind = 0;
     if (field("in_dtype", in) && field("log2_segments", lg) && field("warps", w) && field("tile", tile)) {
       field("kind", kind);  // absent in older files: register form
+      const bool in_ok = in >= 0 && in <= 2;
       const bool shape_ok =
-          kind == es::SEG_KIND_TMA
-              ? (in >= 0 && in <= 2 && w == es::seg_warps_choice((int)in, 2))
-              : (kind == es::SEG_KIND_REGISTER && in >= 0 && in <= 2 &&
-                 (w == es::seg_warps_choice((int)in, 0) || w == es::seg_warps_choice((int)in, 1)));
+          kind == es::SEG_KIND_TMA      ? (in_ok && w == es::seg_warps_choice((int)in, 2))
+          : kind == es::SEG_KIND_WINDOW ? (in_ok && w == es::seg_warps_choice((int)in, 3))
+                                        : (kind == es::SEG_KIND_REGISTER && in_ok &&
+                                           (w == es::seg_warps_choice((int)in, 0) ||
+                                            w == es::seg_warps_choice((int)in, 1)));
       if (in < 0 || in > 2 || lg < 0 || lg > 62 || tile <= 0 || !shape_ok)
         return fail(h, EXACTSUM_EINVAL, "invalid tuning entry");
       es_seg_config c;

@@ -155,29 +155,14 @@ __device__ __forceinline__ TileWork tile_work(const SegArgs& a, int64_t tile) {
   return w;
 }
 
-// After a tile has been added into the warp's columns: regularise, classify,
-// merge the warp carry-free, clear the columns, and either round the segment
-// (a one-tile segment) or add the partial into the segment's accumulator;
-// the warp that retires the last tile rounds it and clears the accumulator.
-template <int DT, int T, int W>
-__device__ __forceinline__ void seg_finish_tile(const SegArgs& a, const TileWork& w, const RangeSplit& r,
-                                                int64_t* digits, int64_t* col, int64_t (*wacc)[ACC_WORDS],
-                                                uint32_t (*wlimbs)[ACC_DIGITS], uint32_t emax) {
-  constexpr int ND = Geometry<DT>::DIGITS;
+// Emit a tile's 80-word warp partial (lane L holds words L, L + 32, L + 64):
+// round the segment at once if this tile is the whole segment, else add it
+// into the segment's accumulator; the warp that retires the last tile of the
+// segment rounds it and clears the accumulator.
+template <int DT, int W>
+__device__ __forceinline__ void seg_emit(const SegArgs& a, const TileWork& w, int64_t d0, int64_t d1, int64_t d2,
+                                         int64_t (*wacc)[ACC_WORDS], uint32_t (*wlimbs)[ACC_DIGITS]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  regularise<DT, T>(col);
-  uint32_t flags = 24u;
-  if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) flags = rescan_split<DT, 32>(a.x, r, lane);
-  flags = __reduce_or_sync(0xffffffffu, flags);
-  __syncwarp();
-
-  // ---- warp merge (carry-free), then clear the columns ----
-  int64_t d0, d1, d2;
-  warp_merge<DT, T>(digits + warp * 32, lane, d0, d1, d2);
-  __syncwarp();
-  for (int i = 0; i < ND; ++i) col[i * T] = 0;
-  if (lane + 64 >= ACC_DIGITS) d2 = (lane + 64 < ACC_WORDS) ? flag_word(lane + 64, flags, w.hi - w.lo) : 0;
-
   if (w.ntiles == 1) {
     wacc[warp][lane] = d0;
     wacc[warp][lane + 32] = d1;
@@ -208,6 +193,32 @@ __device__ __forceinline__ void seg_finish_tile(const SegArgs& a, const TileWork
       __syncwarp();
     }
   }
+}
+
+// After a tile has been added into the warp's columns: regularise, classify,
+// merge the warp carry-free, clear the columns, and either round the segment
+// (a one-tile segment) or add the partial into the segment's accumulator;
+// the warp that retires the last tile rounds it and clears the accumulator.
+template <int DT, int T, int W>
+__device__ __forceinline__ void seg_finish_tile(const SegArgs& a, const TileWork& w, const RangeSplit& r,
+                                                int64_t* digits, int64_t* col, int64_t (*wacc)[ACC_WORDS],
+                                                uint32_t (*wlimbs)[ACC_DIGITS], uint32_t emax) {
+  constexpr int ND = Geometry<DT>::DIGITS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  regularise<DT, T>(col);
+  uint32_t flags = 24u;
+  if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) flags = rescan_split<DT, 32>(a.x, r, lane);
+  flags = __reduce_or_sync(0xffffffffu, flags);
+  __syncwarp();
+
+  // ---- warp merge (carry-free), then clear the columns ----
+  int64_t d0, d1, d2;
+  warp_merge<DT, T>(digits + warp * 32, lane, d0, d1, d2);
+  __syncwarp();
+  for (int i = 0; i < ND; ++i) col[i * T] = 0;
+  if (lane + 64 >= ACC_DIGITS) d2 = (lane + 64 < ACC_WORDS) ? flag_word(lane + 64, flags, w.hi - w.lo) : 0;
+
+  seg_emit<DT, W>(a, w, d0, d1, d2, wacc, wlimbs);
 }
 
 // Register-streaming reducer: each lane loads its own vectors.
@@ -346,6 +357,247 @@ __global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel_tma(SegArgs a) {
   }
 }
 
+// Windowed reducer.  Within one tile the exponents of real data are often
+// concentrated (the paper observes that subtracting the mean leaves a range
+// of about 15 exponents), so each warp keeps, per lane, only a window of
+// WinGeom<DT>::WD digits below the largest digit of the tile's first batch
+// (plus one carry digit), and sends any element that falls outside the
+// window, exactly, into a warp-shared full-width overflow accumulator in the
+// format's native radix (shared-memory integer atomics).  The small columns
+// let many more warps share an SM than the full 66-digit columns do.  Exact
+// for every input; fast when most elements land in the window.
+#ifndef ES_WIN_F64_W
+#define ES_WIN_F64_W 16
+#endif
+#ifndef ES_WIN_U
+#define ES_WIN_U 4
+#endif
+template <int DT> struct WinGeom;
+template <> struct WinGeom<F64> { static constexpr int WD = 4, W = ES_WIN_F64_W; };
+template <> struct WinGeom<F32> { static constexpr int WD = 8, W = 16; };
+template <> struct WinGeom<BF16> { static constexpr int WD = 8, W = 16; };
+
+// Overflow adds per warp between regularisations of an FP64 overflow
+// accumulator: each add changes a digit by less than 2^52, and a check comes
+// at most one batch (32 lanes x 4 vectors x 2 elements) late.
+constexpr int WIN_OVER_REG = 1024;
+
+template <int DT, int W, int U>
+__global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel_win(SegArgs a) {
+  constexpr int T = W * 32;
+  constexpr int WD = WinGeom<DT>::WD;
+  constexpr int NC = WD + 1;                   // window column height (top digit takes carries)
+  constexpr int ND = Geometry<DT>::DIGITS;     // overflow accumulator digits, native radix
+  constexpr int RB = Geometry<DT>::RADIX_BITS;
+  constexpr int EB = Geometry<DT>::ELEM_BYTES;
+  constexpr int EPV = 16 / EB;
+  constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
+  constexpr int64_t PER = (int64_t)32 * U;
+  extern __shared__ int64_t smem_win[];
+  int64_t* cols = smem_win;                    // NC x T
+  int64_t* overflow = smem_win + NC * T;       // W x ND
+  __shared__ int64_t wacc[W][ACC_WORDS];
+  __shared__ uint32_t wlimbs[W][ACC_DIGITS];
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  int64_t* col = cols + t;
+  int64_t* ov = overflow + warp * ND;
+  for (int i = 0; i < NC; ++i) col[i * T] = 0;
+  for (int i = lane; i < ND; i += 32) ov[i] = 0;
+  __syncwarp();
+  const int64_t total = (int64_t)__ldcg((const unsigned long long*)&a.counters[CNT_TOTAL]);
+  if (total > a.map_capacity) return;  // flagged by the planner; results are NaN
+
+  // digit index of an element and its (signed) parts, native radix
+  auto decode = [&](uint64_t bits, int& d, int64_t& lo, int64_t& hi, uint32_t& E) {
+    if constexpr (DT == F64) {
+      const uint32_t lo32 = (uint32_t)bits, hi32 = (uint32_t)(bits >> 32);
+      E = (hi32 >> 20) & 0x7FFu;
+      const uint32_t mhi = (hi32 & 0xFFFFFu) | (E != 0u ? 0x100000u : 0u);
+      const uint32_t p = max(E, 1u) - 1u;
+      const uint32_t w0 = __funnelshift_l(0u, lo32, p);
+      const uint32_t w1 = __funnelshift_l(lo32, mhi, p);
+      const uint32_t w2 = __funnelshift_l(mhi, 0u, p);
+      const int64_t sg = (int64_t)((int32_t)hi32 >> 31);
+      lo = ((int64_t)w0 ^ sg) - sg;
+      hi = ((int64_t)(((uint64_t)w2 << 32) | w1) ^ sg) - sg;
+      d = (int)(p >> 5);
+    } else {
+      constexpr int FB = DT == F32 ? 23 : 7;
+      constexpr uint32_t SIGN = DT == F32 ? 0x80000000u : 0x8000u;
+      const uint32_t w = (uint32_t)bits;
+      E = (w >> FB) & 0xFFu;
+      const uint32_t m = (w & ((1u << FB) - 1u)) | (E != 0u ? (1u << FB) : 0u);
+      const uint32_t p = max(E, 1u) - 1u;
+      const int32_t sg = (w & SIGN) ? -1 : 0;
+      lo = (int64_t)(((int32_t)(m << (p & 7u)) ^ sg) - sg);
+      hi = 0;
+      d = (int)(p >> 3);
+    }
+  };
+  for (;;) {
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(&a.counters[CNT_QUEUE], 1ull);
+    const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, tk, 0);
+    if (tile >= total) break;
+    const TileWork w = tile_work(a, tile);
+    const RangeSplit r = split_range<DT>(a.x, w.lo, w.hi);
+    const uint4* vp = reinterpret_cast<const uint4*>((const char*)a.x + r.vlo * EB);
+    const int64_t cnt = (r.nvec > lane) ? (r.nvec - lane + 31) / 32 : 0;
+    // full batches in which every lane has U vectors: warp-uniform, because
+    // the loop below ends each batch with warp-collective operations
+    const int64_t nb = r.nvec / PER;
+
+    // ---- window base: the largest digit among the first batch of the tile ----
+    uint4 A[U], B[U];
+    // batch k (every lane has U vectors in it) into registers
+    auto fetch = [&](int64_t k, uint4 (&R)[U]) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) R[u] = ldg_stream(vp + lane + k * PER + u * 32);
+    };
+    if (nb > 0) fetch(0, A);
+    uint32_t etop = 0;
+    {
+      auto top_e = [&](uint64_t bits) {
+        int d; int64_t lo, hi; uint32_t E;
+        decode(bits, d, lo, hi, E);
+        if (E != Geometry<DT>::EXP_SPECIAL) etop = max(etop, (uint32_t)d + 1u);
+      };
+      if (nb > 0) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t q[4] = {A[u].x, A[u].y, A[u].z, A[u].w};
+          if constexpr (DT == F64) {
+            top_e(((uint64_t)q[1] << 32) | q[0]);
+            top_e(((uint64_t)q[3] << 32) | q[2]);
+          } else if constexpr (DT == F32) {
+            for (int k = 0; k < 4; ++k) top_e(q[k]);
+          } else {
+            for (int k = 0; k < 4; ++k) {
+              top_e(q[k] & 0xFFFFu);
+              top_e(q[k] >> 16);
+            }
+          }
+        }
+      } else {
+        if (lane < r.head_n) top_e(load_one<DT>(a.x, r.vlo - r.head_n + lane));
+        if (lane < r.tail_n) top_e(load_one<DT>(a.x, r.tail_lo + lane));
+        if (lane < r.nvec)
+          for (int e = 0; e < EPV; ++e) top_e(load_one<DT>(a.x, r.vlo + (int64_t)lane * EPV + e));
+      }
+    }
+    etop = __reduce_max_sync(0xffffffffu, etop);  // top digit + 1 (0: nothing seen)
+    // targets b .. b + WD - 1: FP64 elements need their digit and the one above
+    const int b = (DT == F64) ? max((int)etop + 1 - WD, 0) : max((int)etop - WD, 0);
+
+    uint32_t emax = 0;
+    int reg_left = REG_EVERY;
+    uint32_t nover = 0;  // this lane's overflow adds since the last check
+    auto add_bits = [&](uint64_t bits) {
+      int d; int64_t lo, hi; uint32_t E;
+      decode(bits, d, lo, hi, E);
+      emax = max(emax, E);
+      const unsigned rel = (unsigned)(d - b);
+      if (rel <= (unsigned)(DT == F64 ? WD - 2 : WD - 1)) {
+        col[rel * T] += lo;
+        if constexpr (DT == F64) col[(rel + 1) * T] += hi;
+      } else {
+        atomicAdd((unsigned long long*)&ov[d], (unsigned long long)lo);
+        if constexpr (DT == F64) atomicAdd((unsigned long long*)&ov[d + 1], (unsigned long long)hi);
+        ++nover;
+      }
+    };
+    auto add_vec_w = [&](const uint4& v) {
+      if constexpr (DT == F64) {
+        add_bits(((uint64_t)v.y << 32) | v.x);
+        add_bits(((uint64_t)v.w << 32) | v.z);
+      } else if constexpr (DT == F32) {
+        add_bits(v.x); add_bits(v.y); add_bits(v.z); add_bits(v.w);
+      } else {
+        add_bits(v.x & 0xFFFFu); add_bits(v.x >> 16); add_bits(v.y & 0xFFFFu); add_bits(v.y >> 16);
+        add_bits(v.z & 0xFFFFu); add_bits(v.z >> 16); add_bits(v.w & 0xFFFFu); add_bits(v.w >> 16);
+      }
+    };
+    // keep the window column and the FP64 overflow digits inside int64
+    auto after_batch = [&](int adds) {
+      reg_left -= adds;
+      if (reg_left <= 0) {
+        int64_t carry = 0;
+        for (int i = 0; i < NC - 1; ++i) {
+          const int64_t v = col[i * T] + carry;
+          const int64_t c = (v + ((int64_t)1 << (RB - 1))) >> RB;
+          col[i * T] = v - (c << RB);
+          carry = c;
+        }
+        col[(NC - 1) * T] += carry;
+        reg_left = REG_EVERY;
+      }
+      if constexpr (DT == F64) {
+        const uint32_t warp_over = __reduce_add_sync(0xffffffffu, nover);
+        if (warp_over >= (uint32_t)WIN_OVER_REG) {
+          __syncwarp();
+          if (lane == 0) regularise<DT, 1>(ov);
+          __syncwarp();
+          nover = 0;
+        }
+      }
+    };
+
+    if (lane < r.head_n) add_bits(load_one<DT>(a.x, r.vlo - r.head_n + lane));
+    for (int64_t k = 0; k < nb; k += 2) {
+      if (k + 1 < nb) fetch(k + 1, B);
+#pragma unroll
+      for (int u = 0; u < U; ++u) add_vec_w(A[u]);
+      after_batch(U * EPV);
+      if (k + 1 >= nb) break;
+      if (k + 2 < nb) fetch(k + 2, A);
+#pragma unroll
+      for (int u = 0; u < U; ++u) add_vec_w(B[u]);
+      after_batch(U * EPV);
+    }
+    for (int64_t j = nb * U; j < cnt; ++j) add_vec_w(ldg_stream(vp + lane + j * 32));
+    if (lane < r.tail_n) add_bits(load_one<DT>(a.x, r.tail_lo + lane));
+    after_batch(REG_EVERY);  // forces the window regularisation before the merge
+    // the overflow digits too: the merge below shifts narrow-format digits by
+    // up to 24 bits, so they must be small
+    __syncwarp();
+    if (lane == 0) regularise<DT, 1>(ov);
+
+    uint32_t flags = 24u;
+    if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) flags = rescan_split<DT, 32>(a.x, r, lane);
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    __syncwarp();
+
+    // ---- merge: window columns at offset b plus the overflow accumulator ----
+    const int64_t* wcols = cols + warp * 32;
+    auto native = [&](int n) -> int64_t {  // native-radix digit n of the warp's sum
+      int64_t v = (n < ND) ? ov[n] : 0;
+      const int rel = n - b;
+      if (rel >= 0 && rel < NC) {
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) v += wcols[rel * T + ((k + lane) & 31)];
+      }
+      return v;
+    };
+    auto word = [&](int i) -> int64_t {  // radix-2^32 word i
+      if constexpr (DT == F64) {
+        return native(i);
+      } else {
+        int64_t v = 0;
+        for (int j = 0; j < 4; ++j) v += native(4 * i + j) * ((int64_t)1 << (8 * j));
+        return v;
+      }
+    };
+    int64_t d0 = word(lane), d1 = word(lane + 32), d2 = (lane + 64 < ACC_DIGITS) ? word(lane + 64) : 0;
+    __syncwarp();
+    for (int i = 0; i < NC; ++i) col[i * T] = 0;
+    for (int i = lane; i < ND; i += 32) ov[i] = 0;
+    __syncwarp();
+    if (lane + 64 >= ACC_DIGITS) d2 = (lane + 64 < ACC_WORDS) ? flag_word(lane + 64, flags, w.hi - w.lo) : 0;
+    seg_emit<DT, W>(a, w, d0, d1, d2, wacc, wlimbs);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -394,6 +646,27 @@ static void launch_main_direct(const SegArgs& a, int grid, cudaStream_t st) {
 }
 
 template <int DT>
+constexpr size_t seg_win_smem() {
+  using C = WinGeom<DT>;
+  return (size_t)(C::WD + 1) * C::W * 32 * 8 + (size_t)C::W * Geometry<DT>::DIGITS * 8;
+}
+
+template <int DT>
+static cudaError_t set_attr_win_t() {
+  using C = WinGeom<DT>;
+  static_assert(seg_win_smem<DT>() + (size_t)C::W * (ACC_WORDS * 8 + ACC_DIGITS * 4) <= 232448,
+                "shared memory per CTA");
+  return cudaFuncSetAttribute(seg_sum_kernel_win<DT, C::W, ES_WIN_U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)seg_win_smem<DT>());
+}
+
+template <int DT>
+static void launch_main_win(const SegArgs& a, int grid, cudaStream_t st) {
+  using C = WinGeom<DT>;
+  seg_sum_kernel_win<DT, C::W, ES_WIN_U><<<grid, C::W * 32, seg_win_smem<DT>(), st>>>(a);
+}
+
+template <int DT>
 static void launch_main_tma(const SegArgs& a, int grid, cudaStream_t st) {
   using C = SegTma<DT>;
   seg_sum_kernel_tma<DT, C::W, C::U, C::S><<<grid, C::W * 32, seg_tma_smem<DT>(), st>>>(a);
@@ -412,12 +685,16 @@ static cudaError_t configure_kernels(int dev) {
   if ((e = set_attr_tma_t<F64>()) != cudaSuccess) return e;
   if ((e = set_attr_tma_t<F32>()) != cudaSuccess) return e;
   if ((e = set_attr_tma_t<BF16>()) != cudaSuccess) return e;
+  if ((e = set_attr_win_t<F64>()) != cudaSuccess) return e;
+  if ((e = set_attr_win_t<F32>()) != cudaSuccess) return e;
+  if ((e = set_attr_win_t<BF16>()) != cudaSuccess) return e;
   if (dev >= 0 && dev < 64) done[dev] = true;
   return cudaSuccess;
 }
 
 int seg_warps_choice(int in_dt, int idx) {
   if (idx == 2) return in_dt == F64 ? SegTma<F64>::W : SegTma<F32>::W;
+  if (idx == 3) return in_dt == F64 ? WinGeom<F64>::W : WinGeom<F32>::W;
   if (in_dt == F64) return idx == 0 ? 8 : 12;
   return idx == 0 ? 8 : 16;
 }
@@ -432,6 +709,14 @@ cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int kind, int nu
   seg_scan_kernel<<<1, PLAN_T, 0, st>>>(a, nblocks);
   seg_base_kernel<<<(unsigned)nblocks, PLAN_T, 0, st>>>(a);
   const int grid = num_sms;
+  if (kind == SEG_KIND_WINDOW) {
+    switch (in_dt) {
+      case F64: launch_main_win<F64>(a, grid, st); break;
+      case F32: launch_main_win<F32>(a, grid, st); break;
+      default: launch_main_win<BF16>(a, grid, st); break;
+    }
+    return cudaGetLastError();
+  }
   if (kind == SEG_KIND_TMA) {
     switch (in_dt) {
       case F64: launch_main_tma<F64>(a, grid, st); break;

@@ -28,12 +28,12 @@ struct SegArgs {
 };
 
 // Reducer forms: register streaming (warps choice 0 or 1) or the TMA ring.
-enum : int { SEG_KIND_REGISTER = 0, SEG_KIND_TMA = 1 };
+enum : int { SEG_KIND_REGISTER = 0, SEG_KIND_TMA = 1, SEG_KIND_WINDOW = 2 };
 
 // Enqueue the four kernels of one segmented sum on `st`.
 cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int kind, int num_sms, cudaStream_t st);
 // Warps per CTA of the reducer for a dtype: register form choice 0 or 1;
-// choice 2 is the TMA form's fixed shape.
+// choice 2 is the TMA form's fixed shape, choice 3 the windowed form's.
 int seg_warps_choice(int in_dt, int idx);
 
 }  // namespace es

@@ -147,7 +147,7 @@ def test_autotune_and_tuning_file(tmp_path):
     s = torch.cuda.current_stream().cuda_stream
     warps, kind, tile, ms = es.exactsum_segmented_autotune(h, x.data_ptr(), d_off.data_ptr(), len(lengths),
                                                            es.F64, scratch.data_ptr(), s)
-    assert warps in (8, 12) and kind in (0, 1) and tile > 0 and ms > 0
+    assert warps in (8, 12, 16) and kind in (0, 1, 2) and tile > 0 and ms > 0
     p = str(tmp_path / "tuning.json")
     es.exactsum_tuning_save(h, p)
     text = open(p).read()
@@ -197,29 +197,73 @@ def test_anderson_full_sampled(anderson_full):
         assert int(got_bits[s]) == oracle.exact_sum(seg, threads=16), s
 
 
+REDUCERS = {1: "tma", 2: "window"}
+
+
+def _force_reducer(h, tmp_path, dt, S, kind, tile):
+    lg = int(np.ceil(np.log2(S)))
+    warps = {1: 8 if dt == es.F64 else 12, 2: 16}[kind]
+    p = tmp_path / f"force_{dt}_{kind}_{tile}.json"
+    p.write_text('{"segmented": [{"in_dtype": %d, "log2_segments": %d, "warps": %d, "kind": %d, '
+                 '"tile": %d, "ms": -1}]}' % (dt, lg, warps, kind, tile))
+    es.exactsum_tuning_load(h, str(p))
+
+
+def _restore_default(h, tmp_path, dt, S):
+    lg = int(np.ceil(np.log2(S)))
+    p = tmp_path / f"reg_{dt}.json"
+    p.write_text('{"segmented": [{"in_dtype": %d, "log2_segments": %d, "warps": 8, "kind": 0, "tile": %d}]}'
+                 % (dt, lg, (256 << 10) // es.ITEMSIZE[dt]))
+    es.exactsum_tuning_load(h, str(p))
+
+
+@pytest.mark.parametrize("kind", [1, 2], ids=lambda k: REDUCERS[k])
 @pytest.mark.parametrize("dt", [es.F64, es.F32, es.BF16])
-def test_tma_reducer_forced(tmp_path, dt):
-    """The TMA-ring reducer (chosen through a tuning file) gives the oracle's
-    bits on edge lengths and on random segments, with small and large tiles."""
+def test_reducer_forms_forced(tmp_path, dt, kind):
+    """The TMA-ring and windowed reducers (chosen through a tuning file) give
+    the oracle's bits on edge lengths, with small and large tiles."""
     h = es.handle_for(0)
     lengths = np.array(EDGE_LENGTHS * 3, dtype=np.int64)
     off = W.csr_offsets(lengths) + 1
     bits = make_bits(dt, int(off[-1]) + 3, 40 + dt)
     S = len(lengths)
-    lg = int(np.ceil(np.log2(S)))
-    warps = 8 if dt == es.F64 else 12
-    for tile in (4096, 65536):
-        p = tmp_path / f"tma_{dt}_{tile}.json"
-        p.write_text('{"segmented": [{"in_dtype": %d, "log2_segments": %d, "warps": %d, "kind": 1, '
-                     '"tile": %d, "ms": -1}]}' % (dt, lg, warps, tile))
-        es.exactsum_tuning_load(h, str(p))
-        for o, m in ((dt, es.RNE), (es.F64, es.RUP)):
-            got = run_segmented(bits, off, dt, o, m)
-            want = oracle.exact_sum_segmented(bits, off, dt, o, m, threads=8)
-            assert np.array_equal(got, want.astype(np.uint64)), (tile, o, m)
-    # restore the default choice for this size class
-    p = tmp_path / "reg.json"
-    p.write_text('{"segmented": [{"in_dtype": %d, "log2_segments": %d, "warps": 8, "kind": 0, "tile": %d}]}'
-                 % (dt, lg, (256 << 10) // es.ITEMSIZE[dt]))
-    es.exactsum_tuning_load(h, str(p))
+    try:
+        for tile in (4096, 65536):
+            _force_reducer(h, tmp_path, dt, S, kind, tile)
+            for o, m in ((dt, es.RNE), (es.F64, es.RUP)):
+                got = run_segmented(bits, off, dt, o, m)
+                want = oracle.exact_sum_segmented(bits, off, dt, o, m, threads=8)
+                assert np.array_equal(got, want.astype(np.uint64)), (tile, o, m)
+    finally:
+        _restore_default(h, tmp_path, dt, S)
     assert es.exactsum_device_status(h) & 4 == 0  # no wait timed out
+
+
+@pytest.mark.parametrize("dt", [es.F64, es.F32, es.BF16])
+def test_window_reducer_overflow_path(tmp_path, dt):
+    """Segments whose exponents spread far beyond any window: nearly every
+    element takes the windowed reducer's exact overflow path (and, for FP64,
+    forces many overflow regularisations), and Anderson-style segments that
+    stay inside the window.  Both must match the oracle."""
+    h = es.handle_for(0)
+    lengths = np.array([131072, 3, 200_000, 70_000, 1, 0, 50_000], dtype=np.int64)
+    off = W.csr_offsets(lengths)
+    n = int(off[-1])
+    if dt == es.F64:
+        wide = W.cancelling_f64(n + (n % 2), seed=77, residue=0, emin=-1000, emax=1000)[:n]
+        narrow = W.segmented_f64(lengths, seed=78)
+        cases = (wide, narrow)
+    elif dt == es.F32:
+        cases = (W.wide_f32(n, seed=79), W.uniform_f32(n, seed=80))
+    else:
+        cases = (W.wide_bf16(n, seed=81),)
+    S = len(lengths)
+    try:
+        _force_reducer(h, tmp_path, dt, S, 2, 131072)
+        for bits in cases:
+            for m in (es.RNE, es.RDOWN):
+                got = run_segmented(bits, off, dt, es.F64, m)
+                want = oracle.exact_sum_segmented(bits, off, dt, es.F64, m, threads=8)
+                assert np.array_equal(got, want.astype(np.uint64)), m
+    finally:
+        _restore_default(h, tmp_path, dt, S)
