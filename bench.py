@@ -143,20 +143,79 @@ def measured_traffic(n):
     return d.get("dram_bytes_per_launch")
 
 
-def cpu_baseline(bits, passes: int):
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it (empty if unknown)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return ""
+    for ln in out.splitlines():
+        if ln.strip().startswith("Model name:"):
+            return ln.split(":", 1)[1].strip()
+    return ""
+
+
+def cpu_baseline(bits, passes: int, gpu_bits=None):
     """The CPU oracle, as it stands, on every host core (test infrastructure;
-    timed here only as the reported baseline)."""
+    timed here only as the reported baseline), plus a one-thread time on the
+    first 2^24 elements.  When the GPU result is given, the oracle's result
+    on the same full input is compared with it bit for bit."""
     import oracle
     threads = os.cpu_count() or 1
     oracle.exact_sum(bits[: 1 << 16], threads=threads)  # load + warm
     t0 = time.perf_counter()
     for _ in range(passes):
-        oracle.exact_sum(bits, threads=threads)
+        want = oracle.exact_sum(bits, threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": round(passes * len(bits) / dt / 1e9, 4), "unit": "Gelem/s", "cores": threads,
-            "kind": "oracle",
-            "sample": f"the full 2^{LOG2N}-element workload, {passes} passes, {threads} threads "
-                      f"({dt:.2f} s wall)"}
+    one = bits[: 1 << 24]
+    t1 = time.perf_counter()
+    oracle.exact_sum(one, threads=1)
+    dt1 = time.perf_counter() - t1
+    out = {"value": round(passes * len(bits) / dt / 1e9, 4), "unit": "Gelem/s", "cores": threads,
+           "kind": "oracle",
+           "sample": f"the full 2^{LOG2N}-element workload, {passes} passes, {threads} threads "
+                     f"({dt:.2f} s wall)",
+           "cpu_model": cpu_model(),
+           "single_thread": {"value": round(len(one) / dt1 / 1e9, 4), "unit": "Gelem/s",
+                             "sample": "first 2^24 elements, 1 thread"}}
+    if gpu_bits is not None:
+        out["gpu_result_equals_oracle"] = (gpu_bits & ((1 << 64) - 1)) == want
+    return out
+
+
+def naive_sum_context(torch, x, n, exact_bits, stream):
+    """Context only: the plain FP64 tree reduction (torch.sum) on the same
+    device array, its time and its error against the exact sum, in units in
+    the last place of the exact result (as log2, since it can exceed the
+    FP64 range)."""
+    import struct
+    from fractions import Fraction
+    xf = x.view(torch.float64)
+    for _ in range(3):
+        r = xf.sum()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(10):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = xf.sum()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    ms = times[len(times) // 2]
+    naive = float(r.item())
+    exact = struct.unpack("<d", struct.pack("<Q", exact_bits & ((1 << 64) - 1)))[0]
+    out = {"impl": "torch.sum over the same FP64 array (library tree reduction, not exact)",
+           "ms": round(ms, 4), "Gelem/s": round(n / ms / 1e6, 3), "result": repr(naive),
+           "exact_result": repr(exact)}
+    if math.isfinite(naive) and math.isfinite(exact):
+        err = abs(Fraction(naive) - Fraction(exact))
+        ulp = Fraction(math.ulp(exact))
+        q = err / ulp
+        out["log2_error_ulps"] = round(math.log2(q.numerator) - math.log2(q.denominator), 2) if err else None
+    return out
 
 
 def bench_segmented(es, W, torch, dev, steps, num_segments=65536, per_segment=True):
@@ -315,11 +374,11 @@ def run_reference(args):
         return 0
     from paper_1605_05436_gb300 import workloads as W
     import oracle
-    n = 1 << LOG2N
+    n = 1 << args.log2n
     bits = W.cancelling_f64(n, seed=0)
     threads = os.cpu_count() or 1
     # each step: one pass of the oracle over a bounded sample of the workload
-    sample = bits[: 1 << 26]
+    sample = bits[: 1 << min(26, args.log2n)]
     for _ in range(args.warmup):
         oracle.exact_sum(sample, threads=threads)
     times = []
@@ -334,10 +393,13 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "sample_per_step": len(sample)},
+        "config": {"workload": WORKLOAD if args.log2n == LOG2N
+                   else f"profiling case: n = 2^{args.log2n}, same recipe",
+                   "n": n, "sample_per_step": len(sample)},
         "cpu_baseline": {"value": round(value, 4), "unit": "Gelem/s", "cores": threads,
                          "kind": "oracle",
-                         "sample": f"first 2^26 elements of the workload per step, {threads} threads"},
+                         "sample": f"first {len(sample)} elements of the workload per step, "
+                                   f"{threads} threads"},
         "e2e": {"value": round(value, 4), "unit": "Gelem/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -449,8 +511,9 @@ def run_ours(args):
     }
     if args.log2n != LOG2N:
         line["config"]["workload"] = f"profiling case: n = 2^{args.log2n}, same recipe"
+    line["context"] = {"naive_fp64_sum": naive_sum_context(torch, x, n, result_bits, stream)}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(bits, passes=3)
+        line["cpu_baseline"] = cpu_baseline(bits, passes=3, gpu_bits=result_bits)
     if ws == 1 and args.log2n == LOG2N and not args.primary_only:
         del x
         torch.cuda.empty_cache()
