@@ -270,11 +270,11 @@ def bench_segmented(es, W, torch, dev, steps, num_segments=65536, per_segment=Tr
 
 
 def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_steps=2, max_slots=128):
-    if num_requests <= 0:
-        return None
     """Poisson stream of requests at 20k req/s (mean gap 50 us), sizes
     floor(2^(10 + 16U)), FP64 with p = 0.8 else FP32, windows into 2^26-element
     uniform [-1,1) device pools; served by the continuous-batching engine."""
+    if num_requests <= 0:
+        return None
     req = W.serving_requests(num_requests, seed=0)
     pools = W.serving_pools(26, seed=0)
     d = {es.F64: torch.from_numpy(pools[es.F64].view(np.int64)).to(dev),
@@ -403,6 +403,60 @@ def run_reference(args):
         "e2e": {"value": round(value, 4), "unit": "Gelem/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_narrow(args):
+    """FP32 or BF16 single-array exact sum on the wide-exponent recipes
+    (FP32: n = 2^29, 99% normals with biased exponent uniform in [1, 254] and
+    1% subnormals; BF16: n = 2^30, exponent uniform in [-126, 127]), rounded
+    to the input format: device time and roofline only.  These are parity and
+    profiling cases beside the FP64 benchmark line, not the benchmark."""
+    import torch
+
+    import paper_1605_05436_gb300 as es
+    from paper_1605_05436_gb300 import workloads as W
+
+    dt = {"f32": es.F32, "bf16": es.BF16}[args.dtype]
+    log2n = args.log2n if args.log2n != LOG2N else (29 if dt == es.F32 else 30)
+    n = 1 << log2n
+    eb = 4 if dt == es.F32 else 2
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    es.build()
+    bits = W.wide_f32(n, seed=0) if dt == es.F32 else W.wide_bf16(n, seed=0)
+    x = torch.from_numpy(bits.view(np.int32 if dt == es.F32 else np.int16)).to(dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = es.handle_for(0)
+    for _ in range(max(args.warmup, 3)):
+        es.exactsum_sum(h, x.data_ptr(), n, dt, dt, es.RNE, out.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(0) as clocks:
+        for i in range(args.steps):
+            starts[i].record(stream)
+            es.exactsum_sum(h, x.data_ptr(), n, dt, dt, es.RNE, out.data_ptr(), stream.cuda_stream)
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = n * eb / (ms * 1e-3) / 1e9
+    line = {"metric": f"exact-sum Gelem/s ({args.dtype.upper()}, profiling case)",
+            "value": round(n / ms / 1e6, 3), "unit": "Gelem/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "dtype": "int64" if dt == es.F32 else "int32", "data": "synthetic",
+            "config": {"workload": f"{args.dtype.upper()} n = 2^{log2n}, wide-exponent recipe (seed 0), "
+                                   "rounded to the input format",
+                       "launch": "exactsum_sum, one kernel per step"},
+            "roofline": {"bound": "alu", "hbm_achieved": round(achieved, 1), "hbm_peak": peak,
+                         "unit": "GB/s", "hbm_frac": round(achieved / peak, 4),
+                         "peak_kind": f"{peak_kind} (STREAM-style copy)",
+                         "algorithmic_bytes_per_launch": n * eb},
+            "gpu_launches": args.steps, "clocks": clocks.summary(),
+            "result_bits": f"{int(out.view(torch.int64).item()) & ((1 << (8 * eb)) - 1):#x}"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -545,6 +599,8 @@ def main():
                     help="print the exponent-range sweep over the four dataset families instead")
     ap.add_argument("--requests", type=int, default=100_000,
                     help="requests of the serving measurement (0 skips it)")
+    ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64",
+                    help="f32/bf16: profiling line for the narrow formats instead of the benchmark")
     ap.add_argument("--log2n", type=int, default=LOG2N,
                     help="smaller cases for profiling only; the benchmark line uses 2^28")
     args = ap.parse_args()
@@ -552,6 +608,8 @@ def main():
         return run_reference(args)
     if args.delta_sweep:
         return run_delta_sweep(args)
+    if args.dtype != "f64":
+        return run_narrow(args)
     return run_ours(args)
 
 

@@ -378,7 +378,7 @@ template <> struct WinGeom<F32> { static constexpr int WD = 8, W = 16; };
 template <> struct WinGeom<BF16> { static constexpr int WD = 8, W = 16; };
 
 // Overflow adds per warp between regularisations of an FP64 overflow
-// accumulator: each add changes a digit by less than 2^52, and a check comes
+// accumulator: each add changes a digit by at most 2^52, and a check comes
 // at most one batch (32 lanes x 4 vectors x 2 elements) late.
 constexpr int WIN_OVER_REG = 1024;
 
@@ -418,9 +418,10 @@ __global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel_win(SegArgs a) {
       const uint32_t w0 = __funnelshift_l(0u, lo32, p);
       const uint32_t w1 = __funnelshift_l(lo32, mhi, p);
       const uint32_t w2 = __funnelshift_l(mhi, 0u, p);
-      const int64_t sg = (int64_t)((int32_t)hi32 >> 31);
-      lo = ((int64_t)w0 ^ sg) - sg;
-      hi = ((int64_t)(((uint64_t)w2 << 32) | w1) ^ sg) - sg;
+      // negative: low digit 2^32 - w0, high digit ~(w2:w1) (see add_f64_e)
+      const uint32_t sm = (uint32_t)((int32_t)hi32 >> 31);
+      lo = (int64_t)((uint64_t)(w0 ^ sm) + (hi32 >> 31));
+      hi = (int64_t)(((uint64_t)(w2 ^ sm) << 32) | (w1 ^ sm));
       d = (int)(p >> 5);
     } else {
       constexpr int FB = DT == F32 ? 23 : 7;
