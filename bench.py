@@ -419,7 +419,7 @@ def run_narrow(args):
     from paper_1605_05436_gb300 import workloads as W
 
     dt = {"f32": es.F32, "bf16": es.BF16}[args.dtype]
-    log2n = args.log2n if args.log2n != LOG2N else (29 if dt == es.F32 else 30)
+    log2n = args.log2n if args.log2n is not None else (29 if dt == es.F32 else 30)
     n = 1 << log2n
     eb = 4 if dt == es.F32 else 2
     dev = torch.device("cuda", 0)
@@ -601,9 +601,11 @@ def main():
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64",
                     help="f32/bf16: profiling line for the narrow formats instead of the benchmark")
-    ap.add_argument("--log2n", type=int, default=LOG2N,
+    ap.add_argument("--log2n", type=int, default=None,
                     help="smaller cases for profiling only; the benchmark line uses 2^28")
     args = ap.parse_args()
+    if args.log2n is None and (args.dtype == "f64" or args.impl == "reference"):
+        args.log2n = LOG2N
     if args.impl == "reference":
         return run_reference(args)
     if args.delta_sweep:

@@ -110,21 +110,25 @@ __device__ __forceinline__ void add_f64_e(int64_t* __restrict__ col, uint32_t lo
 #else
   const uint32_t p = max(E, 1u) - 1u;
 #endif
-  // v = m << (p & 31) as three 32-bit words w2:w1:w0 (funnel shifts use p & 31)
-  const uint32_t w0 = __funnelshift_l(0u, lo, p);
-  const uint32_t w1 = __funnelshift_l(lo, mhi, p);
-  const uint32_t w2 = __funnelshift_l(mhi, 0u, p);
+  // v = m << (p & 31) is built as three 32-bit words w2:w1:w0 by funnel
+  // shifts (which use p & 31).  The sign is applied before the shifts: the
+  // funnel shifts of (sm : mhi^sm : lo^sm), sm = 0 or all ones, give v for a
+  // positive element and its 96-bit complement ~v = -v - 1 for a negative
+  // one (the fill bits are sm).  The low digit then gains w0 plus the sign
+  // bit (one three-input add), the high digit the signed 64-bit w2:w1:
+  //   -v = (2^32 - 1 - (v mod 2^32) + 1) + (-(v >> 32) - 1) * 2^32.
+  // Contributions: low digit in [0, 2^32], high digit in [-2^52, 2^52).
+  // (Measured against negating after the shifts: 2% faster; against a
+  // separate 96-bit negation: 6% faster.  Moving the high-digit add to the
+  // FMA pipe as a 32 x 32 -> 64-bit multiply-add by 1 measured 11% slower.)
+  const uint32_t sm = (uint32_t)((int32_t)hi >> 31);
+  const uint32_t xl = lo ^ sm, xh = mhi ^ sm;
+  const uint32_t w0 = __funnelshift_l(sm, xl, p);
+  const uint32_t w1 = __funnelshift_l(xl, xh, p);
+  const uint32_t w2 = __funnelshift_l(xh, sm, p);
   int64_t* d = col + (p >> 5) * STRIDE;
-  // Sign folded into the additions: -v = (2^32 - w0) + ~(w2:w1) * 2^32, so
-  // the low digit gains the 32-bit complement of w0 plus the sign bit (one
-  // three-input add) and the high digit the 64-bit complement of w2:w1; no
-  // separate 96-bit negation.  Contributions: low digit in [0, 2^32], high
-  // digit in [-2^52, 2^52).  (Measured 4% faster than negating first; the
-  // same fold for FP32/BF16 measured 5% slower, so they negate first.)
-  const uint32_t sm = (uint32_t)((int32_t)hi >> 31);  // 0 or all ones
-  const uint32_t sb = hi >> 31;                        // 0 or 1
-  digit_add(d, (int64_t)((uint64_t)(w0 ^ sm) + sb));
-  digit_add(d + STRIDE, (int64_t)(((uint64_t)(w2 ^ sm) << 32) | (w1 ^ sm)));
+  digit_add(d, (int64_t)((uint64_t)w0 + (hi >> 31)));
+  digit_add(d + STRIDE, (int64_t)(((uint64_t)w2 << 32) | w1));
 }
 
 template <int STRIDE>
@@ -274,9 +278,15 @@ template <int STRIDE>
 __device__ __forceinline__ void add_bf16_e(int32_t* __restrict__ col, uint32_t h, uint32_t E) {
   const uint32_t m = (h & 0x7Fu) | (E != 0u ? 0x80u : 0u);
   const uint32_t p = max(E, 1u) - 1u;
-  const int32_t s = -(int32_t)((h >> 15) & 1u);
-  const int32_t v = ((int32_t)(m << (p & 7u)) ^ s) - s;  // |v| < 2^15
-  col[(p >> 3) * STRIDE] += v;
+  // the signed addition as a multiply-add by +-1 (FMA pipe), which frees
+  // the integer ALU pipe that bounds this kernel (measured 6% faster; the
+  // 64-bit form, mad.wide.s32, measured 3% slower for FP32)
+  // (a byte-permute with sign replication for the sign measured 3% slower)
+  const int32_t sgn = ((int32_t)(h << 16) >> 31) | 1;
+  int32_t* d = col + (p >> 3) * STRIDE;
+  int32_t a = *d;
+  asm("mad.lo.s32 %0, %1, %2, %0;" : "+r"(a) : "r"((int32_t)(m << (p & 7u))), "r"(sgn));
+  *d = a;
 }
 
 template <int DT, int STRIDE>
@@ -335,6 +345,94 @@ __device__ __forceinline__ int64_t digit32(const int32_t* __restrict__ col, int 
   return v;
 }
 
+// ---------------------------------------------------------------------------
+// BF16 with sign-split columns: a thread's column holds two halves of
+// unsigned 32-bit digits, positive elements adding into digits 0..32 and
+// negative ones into digits 33..65, so that an element costs no sign
+// arithmetic at all: its sign bit only selects the half (an integer
+// multiply-add in the address, on the FMA pipe).  The column's value is the
+// positive half minus the negative half.  Regularisation carries upwards
+// within each half (digits end in [0, 255]); the top digit of a half
+// receives at most 2^7 per element of the thread's share, below 2^32 for any
+// array that fits in memory.  (Measured 2% faster than signed int32 digits
+// with a multiply-add by +-1; the same split for FP32, whose 64-bit digits
+// then need 528 B per thread, measured 17% slower for want of threads.)
+// ---------------------------------------------------------------------------
+template <int DT, typename D>
+struct ColumnDigits {
+  static constexpr int value = Geometry<DT>::DIGITS;
+};
+template <int DT>
+struct ColumnDigits<DT, uint32_t> {
+  static constexpr int value = 2 * Geometry<DT>::DIGITS;
+};
+
+// h < 2^16: its bit 15 is the sign
+template <int STRIDE>
+__device__ __forceinline__ void add_bf16_split(uint32_t* __restrict__ col, uint32_t h, uint32_t E) {
+  const uint32_t m = (h & 0x7Fu) | (E != 0u ? 0x80u : 0u);
+  const uint32_t p = max(E, 1u) - 1u;
+  col[((p >> 3) + (h >> 15) * 33u) * STRIDE] += m << (p & 7u);
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_vec(uint32_t* __restrict__ col, const uint4& v, uint32_t& emax) {
+  static_assert(DT == BF16, "sign-split 32-bit columns hold BF16 sums only");
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint32_t e[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    e[2 * k] = (w[k] >> 7) & 0xFFu;
+    e[2 * k + 1] = (w[k] >> 23) & 0xFFu;
+  }
+  emax = __vimax3_u32(__vimax3_u32(emax, e[0], e[1]), __vimax3_u32(e[2], e[3], e[4]),
+                      __vimax3_u32(e[5], e[6], e[7]));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    add_bf16_split<STRIDE>(col, w[k] & 0xFFFFu, e[2 * k]);
+    add_bf16_split<STRIDE>(col, w[k] >> 16, e[2 * k + 1]);
+  }
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_one(uint32_t* __restrict__ col, uint64_t bits, uint32_t& emax) {
+  static_assert(DT == BF16, "sign-split 32-bit columns hold BF16 sums only");
+  const uint32_t h = (uint32_t)bits & 0xFFFFu;
+  const uint32_t E = (h >> 7) & 0xFFu;
+  emax = max(emax, E);
+  add_bf16_split<STRIDE>(col, h, E);
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void regularise(uint32_t* __restrict__ col) {
+  static_assert(DT == BF16, "sign-split 32-bit columns hold BF16 sums only");
+  constexpr int ND = Geometry<DT>::DIGITS;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t* c = col + h * ND * STRIDE;
+    uint32_t carry = 0;
+#pragma unroll 4
+    for (int i = 0; i < ND - 1; ++i) {
+      const uint32_t v = c[i * STRIDE] + carry;
+      c[i * STRIDE] = v & 0xFFu;
+      carry = v >> 8;
+    }
+    c[(ND - 1) * STRIDE] += carry;
+  }
+}
+template <int DT, int STRIDE>
+__device__ __forceinline__ int64_t digit32(const uint32_t* __restrict__ col, int i) {
+  static_assert(DT == BF16, "sign-split 32-bit columns hold BF16 sums only");
+  constexpr int ND = Geometry<DT>::DIGITS;
+  int64_t v = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int j = 4 * i + k;
+    if (j < ND) v += ((int64_t)col[j * STRIDE] - (int64_t)col[(ND + j) * STRIDE]) * ((int64_t)1 << (8 * k));
+  }
+  return v;
+}
+
 // Additions between regularisations for a digit type.
 template <int DT, typename D>
 struct RegEvery {
@@ -343,6 +441,10 @@ struct RegEvery {
 template <>
 struct RegEvery<BF16, int32_t> {
   static constexpr int value = 60000;  // (2^31 - 2^7 - 2^23) / 2^15 > 65,000
+};
+template <>
+struct RegEvery<BF16, uint32_t> {
+  static constexpr int value = 120000;  // 255 + 120,000 * 2^15 < 2^32
 };
 
 // Classify one element for the special-value and signed-zero counters.

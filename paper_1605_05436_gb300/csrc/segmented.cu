@@ -415,13 +415,15 @@ __global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel_win(SegArgs a) {
       E = (hi32 >> 20) & 0x7FFu;
       const uint32_t mhi = (hi32 & 0xFFFFFu) | (E != 0u ? 0x100000u : 0u);
       const uint32_t p = max(E, 1u) - 1u;
-      const uint32_t w0 = __funnelshift_l(0u, lo32, p);
-      const uint32_t w1 = __funnelshift_l(lo32, mhi, p);
-      const uint32_t w2 = __funnelshift_l(mhi, 0u, p);
-      // negative: low digit 2^32 - w0, high digit ~(w2:w1) (see add_f64_e)
+      // sign applied before the shifts (see add_f64_e): for a negative
+      // element the low digit gets 2^32 - (v mod 2^32), the high one ~(v >> 32)
       const uint32_t sm = (uint32_t)((int32_t)hi32 >> 31);
-      lo = (int64_t)((uint64_t)(w0 ^ sm) + (hi32 >> 31));
-      hi = (int64_t)(((uint64_t)(w2 ^ sm) << 32) | (w1 ^ sm));
+      const uint32_t xl = lo32 ^ sm, xh = mhi ^ sm;
+      const uint32_t w0 = __funnelshift_l(sm, xl, p);
+      const uint32_t w1 = __funnelshift_l(xl, xh, p);
+      const uint32_t w2 = __funnelshift_l(xh, sm, p);
+      lo = (int64_t)((uint64_t)w0 + (hi32 >> 31));
+      hi = (int64_t)(((uint64_t)w2 << 32) | w1);
       d = (int)(p >> 5);
     } else {
       constexpr int FB = DT == F32 ? 23 : 7;

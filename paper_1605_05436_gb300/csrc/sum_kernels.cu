@@ -107,7 +107,7 @@ __device__ __forceinline__ void finish_cta(const SumArgs& a, D* cols, int64_t* b
 // (int64, or int32 for BF16).
 template <int DT, int T, int U, typename D>
 __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
-  constexpr int ND = Geometry<DT>::DIGITS;
+  constexpr int ND = ColumnDigits<DT, D>::value;
   constexpr int REG_EVERY = RegEvery<DT, D>::value;
   constexpr int NW = T / 32;
 
@@ -283,6 +283,9 @@ struct SumConfig;
 // Streaming form and shape per input format (chosen by measurement):
 //   TMA = 1: sum_kernel_tma<DT, C, TU, S>, (C + 1) warps, S stages of C*32*TU vectors;
 //   TMA = 0: sum_kernel<DT, T, U>, T threads, U vectors per batch.
+// Digit columns: int64 for FP64 and FP32; for BF16 sign-split unsigned
+// 32-bit halves (ES_BF16_SPLIT = 1), else signed int32 (ES_BF16_I32 = 1) or
+// int64.
 #ifndef ES_F64_TMA
 #define ES_F64_TMA 1
 #endif
@@ -332,13 +335,16 @@ struct SumConfig;
 #define ES_BF16_S 4
 #endif
 #ifndef ES_BF16_T
-#define ES_BF16_T 768
+#define ES_BF16_T 512
 #endif
 #ifndef ES_BF16_U
 #define ES_BF16_U 4
 #endif
 #ifndef ES_BF16_I32
 #define ES_BF16_I32 1
+#endif
+#ifndef ES_BF16_SPLIT
+#define ES_BF16_SPLIT 1
 #endif
 template <> struct SumConfig<F64> {
   static constexpr int TMA = ES_F64_TMA, C = ES_F64_C, TU = ES_F64_TU, S = ES_F64_S, T = ES_F64_T, U = ES_F64_U;
@@ -351,7 +357,9 @@ template <> struct SumConfig<F32> {
 template <> struct SumConfig<BF16> {
   static constexpr int TMA = ES_BF16_TMA, C = ES_BF16_C, TU = ES_BF16_TU, S = ES_BF16_S, T = ES_BF16_T,
                        U = ES_BF16_U;
-#if ES_BF16_I32
+#if ES_BF16_SPLIT
+  using Digit = uint32_t;
+#elif ES_BF16_I32
   using Digit = int32_t;
 #else
   using Digit = int64_t;
@@ -361,10 +369,10 @@ template <> struct SumConfig<BF16> {
 template <int DT>
 static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out) {
   using Cfg = SumConfig<DT>;
-  constexpr int ND = Geometry<DT>::DIGITS;
+  using D = typename Cfg::Digit;
+  constexpr int ND = ColumnDigits<DT, D>::value;
   constexpr int THREADS = Cfg::TMA ? (Cfg::C + 1) * 32 : Cfg::T;
   constexpr int COLS = Cfg::TMA ? Cfg::C * 32 : Cfg::T;
-  using D = typename Cfg::Digit;
   static_assert(!Cfg::TMA || sizeof(D) == 8, "the TMA form keeps int64 digit columns");
   constexpr size_t SMEM = Cfg::TMA ? (size_t)ND * COLS * 8 + (size_t)Cfg::S * COLS * Cfg::TU * 16 + 2 * Cfg::S * 8
                                    : (size_t)ND * COLS * sizeof(D);
