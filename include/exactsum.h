@@ -140,6 +140,33 @@ exactsum_status exactsum_sum_host(exactsum_t h, const void* h_x, int64_t n, int 
                                   exactsum_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* Condition-number-sensitive sum (Section 4: r-truncated sparse           */
+/* superaccumulators, r <- r^2 until a stopping condition holds; Section 2: */
+/* sparse and gamma-truncated superaccumulators)                           */
+/* ---------------------------------------------------------------------- */
+
+/* d_result (one element of out_dtype, device) <- the same correctly rounded
+ * sum as exactsum_sum, computed adaptively: pass r (r = 2, 4, 16) keeps in
+ * every thread only the r most significant radix-2^32 digits of its running
+ * sum, counts everything it drops and bounds it by B; the pass stops the
+ * iteration when S - B, S and S + B round to the same value (S the sum of
+ * the truncated partial sums), which then is the rounded exact sum.  When
+ * r reaches the digits the format can occupy (67 FP64, 10 FP32, 9 BF16), the
+ * exact single-pass kernel runs instead (nothing would be truncated).
+ * Work is one pass over d_x per r tried: one pass for well-conditioned
+ * inputs, up to four (FP64) for ill-conditioned ones.
+ *
+ * Synchronous: the host reads each pass's stopping flag, so the call
+ * returns after the result is written (it synchronises `stream`).
+ * passes (host, may be null) <- passes made (>= 1); last_r (host, may be
+ * null) <- r of the pass that stopped, 0 if the exact kernel ran.  Errors
+ * as for exactsum_sum; the handle's per-pass state (64 bytes of device and
+ * page-locked host memory) is allocated on first use. */
+exactsum_status exactsum_sum_adaptive(exactsum_t h, const void* d_x, int64_t n, int in_dtype,
+                                      int out_dtype, int mode, void* d_result, int* passes,
+                                      int* last_r, exactsum_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Accumulators: exact partial sums that persist between calls             */
 /* (Section 2: superaccumulator addition; Section 6.1: reducers write      */
 /* partial accumulators that a post-process merges and rounds)             */
@@ -257,8 +284,10 @@ typedef struct {
  *   chunk_elems: elements of each request processed per step (continuous
  *     batching: every step carries one chunk of every resident request, in
  *     one kernel, so requests that arrive later join at the next step).
- *   tile_elems: elements per warp work unit (multiple of 64 dividing
- *     chunk_elems).
+ *   tile_elems: largest warp work unit in elements (multiple of 64 dividing
+ *     chunk_elems); a chunk is cut into tiles of about chunk / (warps of the
+ *     step kernel), whole multiples of 1,024 elements, at least 2,048 and at
+ *     most tile_elems, so that every chunk is spread over the whole GPU.
  *   max_steps_per_request: if > 0, a request's chunk grows to
  *     ceil(n / max_steps_per_request) (whole tiles) when that is larger than
  *     chunk_elems, so that no request needs more than that many steps; 0

@@ -6,8 +6,10 @@
 //   scheduler -> admit while a slot is free and the budget allows (FIFO);
 //                host-memory requests are staged with an async copy on the
 //                copy stream; build a step with one chunk of every active
-//                request, upload it, launch it, copy the result bits back;
-//                retire steps whose completion event has fired
+//                request (shortest chunks first in tile order), upload it and
+//                launch it; complete each request as soon as the device has
+//                published its result (a sequence number in pinned host
+//                memory); recycle steps whose completion event has fired
 //   poll()    <- completion records (id, status, result bits, timestamps)
 //
 // Up to SERVE_STEPS_IN_FLIGHT steps are in flight, so the host prepares the
@@ -20,6 +22,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstddef>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -63,11 +66,12 @@ struct Req {
 struct StepBuf {
   es::ServeBlock* h_block = nullptr;  // pinned
   es::ServeBlock* d_block = nullptr;
-  uint64_t* h_results = nullptr;      // pinned, max_slots
+  es::ServeDone* h_done = nullptr;    // pinned, SERVE_MAX_ITEMS, written by the device
+  es::ServeDone* d_done = nullptr;    // device alias of h_done
   cudaEvent_t done = nullptr;
   bool busy = false;
   int64_t seq = 0;
-  std::vector<Req*> finals;           // requests that complete in this step
+  std::vector<std::pair<int, Req*>> finals;  // (item, request) completing in this step
 };
 
 }  // namespace
@@ -79,7 +83,6 @@ struct exactsum_server {
   int64_t budget = 0, chunk = 0, tile = 0, max_steps = 0;
   cudaStream_t compute = nullptr, copy = nullptr;
   int64_t* slot_acc = nullptr;
-  uint64_t* d_results = nullptr;
   StepBuf bufs[SERVE_STEPS_IN_FLIGHT];
   int64_t step_seq = 0;
 
@@ -95,6 +98,7 @@ struct exactsum_server {
   std::string error = "no error";               // guarded by mu
   // scheduler-owned
   std::vector<Req*> slots;
+  std::vector<std::pair<int64_t, Req*>> cand;   // chunks of the step being built
   int64_t mem_used = 0;
   int rr = 0;
   std::atomic<int64_t> steps_launched{0};
@@ -154,7 +158,33 @@ void fail_all(exactsum_server* s, const char* what, cudaError_t e) {
   }
 }
 
-// Retire finished steps: report their final requests, free slots.
+// Complete the requests of in-flight steps whose results the device has
+// published (the sequence number is written after the bits, behind a
+// system-scope fence; the acquire fence orders the two reads here).
+bool harvest(exactsum_server* s) {
+  bool progress = false;
+  for (auto& b : s->bufs) {
+    if (!b.busy || b.finals.empty()) continue;
+    for (size_t k = 0; k < b.finals.size();) {
+      const int item = b.finals[k].first;
+      const volatile es::ServeDone* d = b.h_done + item;
+      if (d->seq != (unsigned long long)b.seq) {
+        ++k;
+        continue;
+      }
+      std::atomic_thread_fence(std::memory_order_acquire);
+      Req* r = b.finals[k].second;
+      complete(s, r, EXACTSUM_OK, d->bits);
+      release(s, r);
+      b.finals[k] = b.finals.back();
+      b.finals.pop_back();
+      progress = true;
+    }
+  }
+  return progress;
+}
+
+// Recycle finished steps (after their last results have been harvested).
 bool retire(exactsum_server* s) {
   bool progress = false;
   for (;;) {
@@ -168,11 +198,12 @@ bool retire(exactsum_server* s) {
       fail_all(s, "serving step", q);
       return true;
     }
-    for (Req* r : oldest->finals) {
-      complete(s, r, EXACTSUM_OK, oldest->h_results[r->slot]);
-      release(s, r);
+    harvest(s);
+    if (!oldest->finals.empty()) {
+      // the step has finished but a final item published nothing
+      fail_all(s, "serving step finished without publishing a result", cudaErrorUnknown);
+      return true;
     }
-    oldest->finals.clear();
     oldest->busy = false;
     progress = true;
   }
@@ -237,6 +268,17 @@ bool admit(exactsum_server* s) {
   return progress;
 }
 
+// Elements per tile of a chunk: one warp streams one tile at a few GB/s, so
+// a chunk is spread over all the step kernel's warps (tiles of len / warps,
+// whole multiples of 1,024 elements), between 2,048 elements (below which the
+// per-tile merge dominates) and the engine's tile.
+int64_t chunk_tile(const exactsum_server* s, int64_t len) {
+  const int64_t warps = (int64_t)s->num_sms * es::SERVE_WARPS_PER_CTA;
+  int64_t t = (len + warps - 1) / warps;
+  t = (t + 1023) / 1024 * 1024;
+  return std::min(s->tile, std::max<int64_t>(t, 2048));
+}
+
 bool launch_step(exactsum_server* s) {
   StepBuf* b = nullptr;
   for (auto& c : s->bufs)
@@ -245,18 +287,31 @@ bool launch_step(exactsum_server* s) {
       break;
     }
   if (!b) return false;
+  // one chunk of every active request; shortest first in tile order, so that
+  // small requests are rounded (and published) early in the step
+  auto& cand = s->cand;
+  cand.clear();
+  for (int k = 0; k < s->max_slots && (int)cand.size() < es::SERVE_MAX_ITEMS; ++k) {
+    Req* r = s->slots[(s->rr + k) % s->max_slots];
+    if (r && r->pos < r->n) cand.emplace_back(std::min(r->chunk, r->n - r->pos), r);
+  }
+  if (cand.empty()) return false;
+  std::stable_sort(cand.begin(), cand.end(),
+                   [](const std::pair<int64_t, Req*>& a, const std::pair<int64_t, Req*>& c) {
+                     return a.first < c.first;
+                   });
+  const int64_t seq = s->step_seq + 1;
   int nitems = 0;
   int64_t tiles = 0;
-  for (int k = 0; k < s->max_slots && nitems < es::SERVE_MAX_ITEMS; ++k) {
-    const int i = (s->rr + k) % s->max_slots;
-    Req* r = s->slots[i];
-    if (!r || r->pos >= r->n) continue;
-    const int64_t len = std::min(r->chunk, r->n - r->pos);
+  for (auto& cr : cand) {
+    Req* r = cr.second;
+    const int64_t len = cr.first;
     es::ServeItem& it = b->h_block->items[nitems];
     it.x = r->xd + r->pos * elem_bytes(r->in);
     it.len = len;
+    it.tile = chunk_tile(s, len);
     it.tile_base = tiles;
-    it.ntiles = (len + s->tile - 1) / s->tile;
+    it.ntiles = (len + it.tile - 1) / it.tile;
     it.slot = r->slot;
     it.in = r->in;
     it.out = r->out;
@@ -270,32 +325,31 @@ bool launch_step(exactsum_server* s) {
       r->fresh = false;
     }
     r->pos += len;
-    if (it.final) b->finals.push_back(r);
+    if (it.final) b->finals.emplace_back(nitems, r);
     ++nitems;
   }
-  if (nitems == 0) return false;
   s->rr = (s->rr + 1) % s->max_slots;
   b->h_block->queue = 0;
-  cudaError_t e = cudaMemcpyAsync(b->d_block, b->h_block, sizeof(es::ServeBlock), cudaMemcpyHostToDevice, s->compute);
+  // the block up to the last used item (the counters precede the items)
+  const size_t bytes = offsetof(es::ServeBlock, items) + (size_t)nitems * sizeof(es::ServeItem);
+  cudaError_t e = cudaMemcpyAsync(b->d_block, b->h_block, bytes, cudaMemcpyHostToDevice, s->compute);
   es::ServeStep st;
   st.items = b->d_block->items;
   st.nitems = nitems;
-  st.tile = s->tile;
   st.remaining = b->d_block->remaining;
   st.queue = &b->d_block->queue;
   st.slot_acc = s->slot_acc;
-  st.results = s->d_results;
+  st.done = b->d_done;
+  st.seq = (unsigned long long)seq;
   if (e == cudaSuccess) e = es::serve_launch(st, s->num_sms, s->compute);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->h_results, s->d_results, (size_t)s->max_slots * sizeof(uint64_t),
-                        cudaMemcpyDeviceToHost, s->compute);
   if (e == cudaSuccess) e = cudaEventRecord(b->done, s->compute);
   if (e != cudaSuccess) {
     fail_all(s, "serving launch", e);
     return true;
   }
   b->busy = true;
-  b->seq = ++s->step_seq;
+  b->seq = seq;
+  s->step_seq = seq;
   s->steps_launched.fetch_add(1);
   return true;
 }
@@ -303,7 +357,8 @@ bool launch_step(exactsum_server* s) {
 void scheduler(exactsum_server* s) {
   cudaSetDevice(s->device);
   while (!s->failed.load()) {
-    bool progress = retire(s);
+    bool progress = harvest(s);
+    progress |= retire(s);
     if (s->failed.load()) break;
     progress |= admit(s);
     progress |= launch_step(s);
@@ -336,12 +391,11 @@ exactsum_status server_fail(exactsum_server* s, exactsum_status st, const std::s
 void server_free(exactsum_server* s) {
   for (auto& b : s->bufs) {
     if (b.h_block) cudaFreeHost(b.h_block);
-    if (b.h_results) cudaFreeHost(b.h_results);
+    if (b.h_done) cudaFreeHost(b.h_done);
     cudaFree(b.d_block);
     if (b.done) cudaEventDestroy(b.done);
   }
   cudaFree(s->slot_acc);
-  cudaFree(s->d_results);
   if (s->compute) cudaStreamDestroy(s->compute);
   if (s->copy) cudaStreamDestroy(s->copy);
 }
@@ -377,10 +431,12 @@ exactsum_status exactsum_server_create(exactsum_server_t* out, int device, int m
   ok = ok && cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaMalloc(&s->slot_acc, (size_t)max_slots * es::ACC_WORDS * sizeof(int64_t)) == cudaSuccess;
   ok = ok && cudaMemset(s->slot_acc, 0, (size_t)max_slots * es::ACC_WORDS * sizeof(int64_t)) == cudaSuccess;
-  ok = ok && cudaMalloc(&s->d_results, (size_t)max_slots * sizeof(uint64_t)) == cudaSuccess;
   for (auto& b : s->bufs) {
     ok = ok && cudaMallocHost(&b.h_block, sizeof(es::ServeBlock)) == cudaSuccess;
-    ok = ok && cudaMallocHost(&b.h_results, (size_t)max_slots * sizeof(uint64_t)) == cudaSuccess;
+    ok = ok && cudaHostAlloc(&b.h_done, es::SERVE_MAX_ITEMS * sizeof(es::ServeDone), cudaHostAllocMapped) ==
+                   cudaSuccess;
+    if (ok) std::memset(b.h_done, 0, es::SERVE_MAX_ITEMS * sizeof(es::ServeDone));
+    ok = ok && cudaHostGetDevicePointer((void**)&b.d_done, b.h_done, 0) == cudaSuccess;
     ok = ok && cudaMalloc(&b.d_block, sizeof(es::ServeBlock)) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) == cudaSuccess;
   }

@@ -8,8 +8,9 @@
 // free).  The slot accumulator lives on the device for the whole life of
 // the request, across steps (the reducer state of Section 6.1 kept on the
 // device).  The warp that retires the last tile of a request's final chunk
-// rounds the slot (Section 3 steps 6-7), writes the result and clears the
-// slot.
+// rounds the slot (Section 3 steps 6-7), clears it and publishes the result
+// to the host at once (pinned memory, system-scope fence, then a sequence
+// number), so that a request never waits for the other chunks of its step.
 #include <cuda_runtime.h>
 
 #include "digits.cuh"
@@ -19,7 +20,7 @@
 
 namespace es {
 
-constexpr int SERVE_W = 8;         // warps per CTA
+constexpr int SERVE_W = SERVE_WARPS_PER_CTA;
 constexpr int SERVE_T = SERVE_W * 32;
 constexpr int SERVE_U = 4;
 constexpr int SERVE_ND = Geometry<F64>::DIGITS;  // column height (FP64 is the tallest)
@@ -71,8 +72,8 @@ __global__ void __launch_bounds__(SERVE_T, 1) serve_step_kernel(ServeStep st) {
       else hi_i = mid - 1;
     }
     const ServeItem it = st.items[lo_i];
-    const int64_t lo = (tile - it.tile_base) * st.tile;
-    const int64_t hi = min(it.len, lo + st.tile);
+    const int64_t lo = (tile - it.tile_base) * it.tile;
+    const int64_t hi = min(it.len, lo + it.tile);
     int64_t d0, d1, d2;
     uint32_t flags = 0;
     int64_t* warp_cols = digits + warp * 32;
@@ -101,7 +102,10 @@ __global__ void __launch_bounds__(SERVE_T, 1) serve_step_kernel(ServeStep st) {
       __syncwarp();
       if (lane == 0) {
         const uint64_t bits = finalize_acc(wacc[warp], wlimbs[warp], it.in, it.out, it.mode);
-        st.results[it.slot] = bits;
+        volatile ServeDone* d = st.done + lo_i;
+        d->bits = bits;
+        __threadfence_system();
+        d->seq = st.seq;
       }
       __syncwarp();
     }

@@ -128,9 +128,10 @@ def _constant_device(bits_value: int, n: int, dt: int):
 def test_regularisation_bound(dt, n):
     """Adversarial inputs at the deferred-carry headroom: every element adds
     the largest possible value to one digit (mantissa all ones at the
-    largest in-digit offset), all of one sign and then with alternating
-    signs.  n is large enough that each thread regularises mid-stream.  The
-    exact sums are closed forms (n * x and x), rounded by the oracle."""
+    largest in-digit offset), all positive, all negative, and then with
+    alternating signs.  n is large enough that each thread regularises
+    mid-stream.  The exact sums are closed forms (n * x, -n * x and x),
+    rounded by the oracle."""
     if dt == es.F64:
         v, unit, m, p = (1024 << 52) | ((1 << 52) - 1), -1074, (1 << 53) - 1, 1023   # p = 32*31 + 31
     elif dt == es.F32:
@@ -144,7 +145,12 @@ def test_regularisation_bound(dt, n):
         torch.cuda.synchronize()
         assert G.result_bits(r, o)[0] == oracle.round_value(n * (m << p), unit, o, es.RNE), o
     neg = _constant_device(v | sign, 1, dt)
-    x[1::2] = neg[0]  # alternate signs: n is odd, so the sum is x itself
+    x.fill_(neg[0])
+    for o in (dt, es.F64):
+        r = es.exact_sum(x, o, es.RNE)
+        torch.cuda.synchronize()
+        assert G.result_bits(r, o)[0] == oracle.round_value(-n * (m << p), unit, o, es.RNE), o
+    x[0::2] = _constant_device(v, 1, dt)[0]  # alternate signs: n is odd, so the sum is x itself
     r = es.exact_sum(x, dt, es.RNE)
     torch.cuda.synchronize()
     assert G.result_bits(r, dt)[0] == v
