@@ -325,6 +325,43 @@ def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_st
                        "steps": stats["steps"], "peak_resident": stats["peak_active"]}}
 
 
+def bench_adaptive(es, torch, dev, x, n, reps=3):
+    """The condition-number-sensitive path (r-truncated passes, r <- r^2)
+    beside the exact single pass, on the benchmark input and on a
+    well-conditioned one of the same size: passes needed and wall time of
+    the synchronous call (median of ``reps`` after one warm-up)."""
+    h = es.handle_for(dev.index)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize(dev)
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts) * 1e3, r
+
+    res = {}
+    uni = (torch.rand(n, dtype=torch.float64, device=dev) * 2 - 1).view(torch.int64)
+    for name, arr in (("cancelling delta~2000 (the benchmark input)", x),
+                      ("uniform [-1,1) (device-generated)", uni)):
+        ms_a, (passes, last_r) = timed(lambda: es.exactsum_sum_adaptive(
+            h, arr.data_ptr(), n, es.F64, es.F64, es.RNE, out.data_ptr(), s))
+        bits_a = int(out.view(torch.int64).item())
+        ms_e, _ = timed(lambda: es.exactsum_sum(h, arr.data_ptr(), n, es.F64, es.F64, es.RNE,
+                                                out.data_ptr(), s))
+        bits_e = int(out.view(torch.int64).item())
+        res[name] = {"passes": passes, "last_r": last_r, "adaptive_ms": round(ms_a, 3),
+                     "exact_ms": round(ms_e, 3), "same_result": bits_a == bits_e}
+    del uni
+    return {"n": n, "api": "exactsum_sum_adaptive (synchronous; r = 2, 4, 16, then the exact pass)",
+            "workloads": res}
+
+
 def run_delta_sweep(args):
     """Throughput of the FP64 exact sum over the paper's four dataset families
     and exponent ranges delta (the design of the paper's Fig. 2 experiment,
@@ -569,6 +606,7 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(bits, passes=3, gpu_bits=result_bits)
     if ws == 1 and args.log2n == LOG2N and not args.primary_only:
+        line["adaptive"] = bench_adaptive(es, torch, dev, x, n)
         del x
         torch.cuda.empty_cache()
         line["segmented"] = bench_segmented(es, W, torch, dev, args.steps, args.segments,

@@ -6,6 +6,7 @@ and by the CPU-baseline leg of ``bench.py``.  The library under
 """
 from .oracle import (build, exact_sum, exact_sum_segmented, exact_value, round_value,
                      F64, F32, BF16, RNE, RTZ, RUP, RDOWN)
+from .adaptive import adaptive_sum
 
-__all__ = ["build", "exact_sum", "exact_sum_segmented", "exact_value", "round_value",
+__all__ = ["build", "exact_sum", "exact_sum_segmented", "exact_value", "round_value", "adaptive_sum",
            "F64", "F32", "BF16", "RNE", "RTZ", "RUP", "RDOWN"]

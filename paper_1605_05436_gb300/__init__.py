@@ -42,6 +42,8 @@ _SIGNATURES = {
     "exactsum_destroy": [_vp],
     "exactsum_sum": [_vp, _vp, _i64, _int, _int, _int, _vp, _vp],
     "exactsum_sum_host": [_vp, _vp, _i64, _int, _int, _int, _vp, _vp],
+    "exactsum_sum_adaptive": [_vp, _vp, _i64, _int, _int, _int, _vp, ctypes.POINTER(_int),
+                              ctypes.POINTER(_int), _vp],
     "exactsum_acc_zero": [_vp, _vp, _vp],
     "exactsum_acc_add": [_vp, _vp, _i64, _int, _vp, _vp],
     "exactsum_acc_round": [_vp, _vp, _int, _int, _int, _vp, _vp],
@@ -142,6 +144,14 @@ def exactsum_sum(handle, d_x, n, in_dtype, out_dtype, mode, d_result, stream) ->
 def exactsum_sum_host(handle, h_x, n, in_dtype, out_dtype, mode, h_result, stream) -> None:
     _check(library().exactsum_sum_host(handle, h_x, n, in_dtype, out_dtype, mode, h_result, stream),
            handle)
+
+
+def exactsum_sum_adaptive(handle, d_x, n, in_dtype, out_dtype, mode, d_result, stream) -> tuple:
+    """Returns (passes, last_r) (last_r 0 when the exact kernel ran)."""
+    passes, last_r = _int(0), _int(0)
+    _check(library().exactsum_sum_adaptive(handle, d_x, n, in_dtype, out_dtype, mode, d_result,
+                                           ctypes.byref(passes), ctypes.byref(last_r), stream), handle)
+    return passes.value, last_r.value
 
 
 def exactsum_acc_zero(handle, d_acc, stream) -> None:
@@ -326,6 +336,22 @@ def exact_sum(x, out_dtype: int | None = None, mode: int = RNE, stream=None, out
     exactsum_sum(handle_for(dev), x.data_ptr() if x.numel() else None, x.numel(), in_dtype,
                  out_dtype, mode, out.data_ptr(), _stream_ptr(stream, dev))
     return out
+
+
+def adaptive_sum(x, out_dtype: int | None = None, mode: int = RNE, stream=None, out=None):
+    """The condition-number-sensitive sum of a contiguous CUDA tensor (the
+    same correctly rounded result as exact_sum); returns (result tensor,
+    passes, last_r)."""
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("adaptive_sum takes a contiguous CUDA tensor")
+    in_dtype = dtype_code(x)
+    out_dtype = in_dtype if out_dtype is None else out_dtype
+    dev = x.device.index
+    if out is None:
+        out = result_tensor(out_dtype, x.device)
+    passes, last_r = exactsum_sum_adaptive(handle_for(dev), x.data_ptr() if x.numel() else None, x.numel(),
+                                           in_dtype, out_dtype, mode, out.data_ptr(), _stream_ptr(stream, dev))
+    return out, passes, last_r
 
 
 def exact_sum_host(x, out_dtype: int | None = None, mode: int = RNE, device: int = 0, stream=None):

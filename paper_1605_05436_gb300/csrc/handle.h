@@ -57,6 +57,10 @@ struct exactsum_ctx {
   void* d_result_tmp = nullptr;     // 8 bytes
   void* h_result_pinned = nullptr;  // 8 bytes, page-locked
 
+  // condition-number-sensitive sum (truncated.cu): per-pass state
+  unsigned long long* trunc_state = nullptr;       // device, 8 words
+  unsigned long long* trunc_state_host = nullptr;  // page-locked copy
+
   // segmented workspace (see segmented.cu)
   int64_t seg_capacity = 0;
   int64_t* seg_acc = nullptr;       // seg_capacity x ACC_WORDS, zero between calls

@@ -1,0 +1,410 @@
+// truncated.cu -- the condition-number-sensitive sum (Section 4, the r <- r^2
+// iteration over r-truncated sparse superaccumulators; Section 2, sparse and
+// gamma-truncated superaccumulators).
+//
+// One pass with truncation parameter R:
+//   1. every thread keeps a window of the R most significant radix-2^32
+//      digits of its running sum in shared memory (the r-truncated sparse
+//      superaccumulator of its chain of additions: a left-deep summation
+//      tree).  An element is split into two digit parts; a part above the
+//      window moves the window up (the digits that fall out of the bottom are
+//      dropped), a part below the window is dropped;
+//   2. every dropped item is counted, together with the highest digit index
+//      ever dropped: a dropped element part at digit j is smaller than
+//      2^(32j + 52) units, a dropped window digit (regularised first) smaller
+//      than 2^(32j + 32), so the total truncated mass is at most
+//      B = events * 2^(32 * maxdrop + 52) units;
+//   3. the threads' windows are merged exactly (CTA, then the last CTA over
+//      the CTAs' partials) into S, the sum of the truncated chains;
+//   4. stopping condition: the last CTA rounds S - B, S and S + B; when the
+//      three agree, every value within B of S -- the exact sum among them --
+//      rounds to the same result, which is returned and the iteration stops.
+//      This is the paper's test that the result is unchanged by adding or
+//      subtracting a bound of everything truncated, taken on the unrounded
+//      sum so that the result is the correctly rounded exact sum.
+// The host runs R = 2, 4, 16 (r <- r^2 from r = 2) and, when R reaches the
+// digits a format can occupy (67 for FP64, 10 for FP32, 9 for BF16), the
+// exact single-pass kernel, which is the untruncated case.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "../../include/exactsum.h"
+#include "digits.cuh"
+#include "finalize.cuh"
+#include "handle.h"
+#include "internal.h"
+#include "stream.cuh"
+
+namespace es {
+
+struct TruncArgs {
+  const void* x;
+  int64_t n, head, nvec, tail;
+  int out, mode;
+  void* result;
+  int64_t* partials;             // grid x ACC_WORDS
+  unsigned int* ticket;          // zero between launches; reset by the last CTA
+  unsigned long long* state;     // [0] events, [1] highest dropped digit + 1, [2] stop (zeroed by the host)
+};
+
+constexpr int TR_T = 512;  // threads per CTA
+constexpr int TR_U = 4;    // 16-byte vectors per thread per batch
+constexpr int TR_REG_EVERY = 1984;  // digit parts between window regularisations (each < 2^52)
+
+// An element as two radix-2^32 digit parts: value = lo * 2^(32k) + hi * 2^(32(k+1))
+// units, lo in [0, 2^32], hi in [-2^52, 2^52) (the sign folded as in add_f64_e).
+template <int DT>
+__device__ __forceinline__ void split32(uint64_t bits, int& k, int64_t& lo, int64_t& hi) {
+  uint32_t mlo, mhi, p, neg;
+  if constexpr (DT == F64) {
+    const uint32_t l = (uint32_t)bits, h = (uint32_t)(bits >> 32);
+    const uint32_t E = (h >> 20) & 0x7FFu;
+    mlo = l;
+    mhi = (h & 0xFFFFFu) | (E != 0u ? 0x100000u : 0u);
+    p = max(E, 1u) - 1u;
+    neg = h >> 31;
+  } else if constexpr (DT == F32) {
+    const uint32_t w = (uint32_t)bits;
+    const uint32_t E = (w >> 23) & 0xFFu;
+    mlo = (w & 0x7FFFFFu) | (E != 0u ? 0x800000u : 0u);
+    mhi = 0;
+    p = max(E, 1u) - 1u;
+    neg = w >> 31;
+  } else {
+    const uint32_t w = (uint32_t)bits & 0xFFFFu;
+    const uint32_t E = (w >> 7) & 0xFFu;
+    mlo = (w & 0x7Fu) | (E != 0u ? 0x80u : 0u);
+    mhi = 0;
+    p = max(E, 1u) - 1u;
+    neg = w >> 15;
+  }
+  const uint32_t sm = 0u - neg;
+  const uint32_t xl = mlo ^ sm, xh = mhi ^ sm;
+  const uint32_t w0 = __funnelshift_l(sm, xl, p);
+  const uint32_t w1 = __funnelshift_l(xl, xh, p);
+  const uint32_t w2 = __funnelshift_l(xh, sm, p);
+  k = (int)(p >> 5);
+  lo = (int64_t)((uint64_t)w0 + neg);
+  hi = (int64_t)(((uint64_t)w2 << 32) | w1);
+}
+
+// The R-digit window of one thread: digit i (top - R < i <= top) lives in
+// slot i mod R of the thread's column (slot s at col[s * TR_T]).
+template <int R>
+struct Window {
+  int64_t* col;
+  int top;                     // most significant digit held; -1 while empty
+  unsigned long long events;   // items dropped
+  int maxdrop;                 // highest digit index dropped; -1 if none
+  int adds;                    // parts added since the last regularisation
+
+  __device__ __forceinline__ int64_t& slot(int i) { return col[(i & (R - 1)) * TR_T]; }
+
+  __device__ __forceinline__ void drop(int j) {
+    ++events;
+    maxdrop = max(maxdrop, j);
+  }
+
+  // Lemma 1 carries inside the window (balanced digits); a carry out of the
+  // top digit moves the window up by one.
+  __device__ void regularise() {
+    adds = 0;
+    if (top < 0) return;
+    int64_t carry = 0;
+#pragma unroll
+    for (int i = top - R + 1; i <= top; ++i) {
+      const int64_t v = slot(i) + carry;
+      const int64_t c = (v + ((int64_t)1 << 31)) >> 32;
+      slot(i) = v - (c << 32);
+      carry = c;
+    }
+    if (carry != 0) {
+      int64_t& s = slot(top + 1);  // holds digit top + 1 - R, now leaving the window
+      if (s != 0) drop(top + 1 - R);
+      s = carry;
+      ++top;
+    }
+  }
+
+  // Move the window up so that its top digit is t (> top).
+  __device__ void raise(int t) {
+    regularise();
+    if (t <= top) return;
+    if (t - top >= R) {
+#pragma unroll
+      for (int i = top - R + 1; i <= top; ++i)
+        if (slot(i) != 0) {
+          drop(i);
+          slot(i) = 0;
+        }
+    } else {
+      for (int i = top + 1; i <= t; ++i) {
+        int64_t& s = slot(i);  // holds digit i - R
+        if (s != 0) {
+          drop(i - R);
+          s = 0;
+        }
+      }
+    }
+    top = t;
+  }
+
+  __device__ __forceinline__ void add(int j, int64_t v) {
+    if (v == 0) return;
+    if (top < 0) top = j;
+    else if (j > top) raise(j);
+    if (j <= top - R) {
+      drop(j);
+      return;
+    }
+    slot(j) += v;
+    if (++adds >= TR_REG_EVERY) regularise();
+  }
+
+  __device__ __forceinline__ int64_t digit(int i) const {
+    return (top >= 0 && i <= top && i > top - R) ? col[(i & (R - 1)) * TR_T] : 0;
+  }
+};
+
+template <int DT, int R>
+__device__ __forceinline__ void add_elem(Window<R>& w, uint64_t bits, uint32_t& emax) {
+  constexpr int FB = DT == F64 ? 52 : (DT == F32 ? 23 : 7);
+  constexpr uint64_t EM = (uint64_t)Geometry<DT>::EXP_SPECIAL;
+  emax = max(emax, (uint32_t)((bits >> FB) & EM));
+  int k;
+  int64_t lo, hi;
+  split32<DT>(bits, k, lo, hi);
+  w.add(k + 1, hi);
+  w.add(k, lo);
+}
+
+template <int DT, int R>
+__device__ __forceinline__ void add_vec16(Window<R>& w, const uint4& v, uint32_t& emax) {
+  if constexpr (DT == F64) {
+    add_elem<DT, R>(w, ((uint64_t)v.y << 32) | v.x, emax);
+    add_elem<DT, R>(w, ((uint64_t)v.w << 32) | v.z, emax);
+  } else if constexpr (DT == F32) {
+    add_elem<DT, R>(w, v.x, emax);
+    add_elem<DT, R>(w, v.y, emax);
+    add_elem<DT, R>(w, v.z, emax);
+    add_elem<DT, R>(w, v.w, emax);
+  } else {
+    const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      add_elem<DT, R>(w, q[k] & 0xFFFFu, emax);
+      add_elem<DT, R>(w, q[k] >> 16, emax);
+    }
+  }
+}
+
+template <int DT, int R>
+__global__ void __launch_bounds__(TR_T, 1) trunc_sum_kernel(TruncArgs a) {
+  constexpr int EB = Geometry<DT>::ELEM_BYTES;
+  constexpr int EPV = 16 / EB;
+  constexpr int NW = TR_T / 32;
+  extern __shared__ int64_t tr_cols[];  // R x TR_T
+  __shared__ int tops[TR_T];
+  __shared__ int64_t blk[ACC_WORDS];
+  __shared__ int64_t tmp[ACC_WORDS];
+  __shared__ uint32_t limbs[ACC_DIGITS];
+  __shared__ uint32_t blk_flags, is_last;
+  __shared__ unsigned long long blk_events;
+  __shared__ int blk_maxdrop;
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t G = gridDim.x;
+  if (t == 0) {
+    blk_flags = 0;
+    blk_events = 0;
+    blk_maxdrop = -1;
+  }
+  Window<R> w;
+  w.col = tr_cols + t;
+  w.top = -1;
+  w.events = 0;
+  w.maxdrop = -1;
+  w.adds = 0;
+#pragma unroll
+  for (int s = 0; s < R; ++s) w.col[s * TR_T] = 0;
+
+  // this thread's vectors vb + t + j*T (the same ownership as the exact kernel)
+  const uint4* vx = reinterpret_cast<const uint4*>((const char*)a.x + a.head * EB);
+  const int64_t vb = a.nvec * blockIdx.x / G, ve = a.nvec * (blockIdx.x + 1) / G;
+  uint32_t emax = 0;
+  const int64_t cnt = (vb + t < ve) ? (ve - vb - t + TR_T - 1) / TR_T : 0;
+  const uint4* p = vx + vb + t;
+  const int64_t nb = cnt / TR_U;
+  uint4 A[TR_U];
+  for (int64_t k = 0; k < nb; ++k) {
+#pragma unroll
+    for (int u = 0; u < TR_U; ++u) A[u] = ldg_stream(p + (k * TR_U + u) * TR_T);
+#pragma unroll
+    for (int u = 0; u < TR_U; ++u) add_vec16<DT, R>(w, A[u], emax);
+  }
+  for (int64_t j = nb * TR_U; j < cnt; ++j) add_vec16<DT, R>(w, ldg_stream(p + j * TR_T), emax);
+  if (blockIdx.x == 0 && t < a.head) add_elem<DT, R>(w, load_one<DT>(a.x, t), emax);
+  if (blockIdx.x == G - 1 && t < a.tail) add_elem<DT, R>(w, load_one<DT>(a.x, a.n - a.tail + t), emax);
+  w.regularise();
+  tops[t] = w.top;
+
+  // special values and signed zeros: exact rescan only when needed
+  uint32_t flags = 24u;
+  if (emax == Geometry<DT>::EXP_SPECIAL || emax == 0u) {
+    flags = 0;
+    const char* base = (const char*)a.x + a.head * EB;
+    for (int64_t v = vb + t; v < ve; v += TR_T)
+      for (int e = 0; e < EPV; ++e) flags |= classify<DT>(load_one<DT>(base, v * EPV + e));
+    if (blockIdx.x == 0 && t < a.head) flags |= classify<DT>(load_one<DT>(a.x, t));
+    if (blockIdx.x == G - 1 && t < a.tail) flags |= classify<DT>(load_one<DT>(a.x, a.n - a.tail + t));
+  }
+  __syncthreads();
+  if (flags) atomicOr(&blk_flags, flags);
+  if (w.events) atomicAdd(&blk_events, w.events);
+  if (w.maxdrop >= 0) atomicMax(&blk_maxdrop, w.maxdrop);
+
+  // ---- CTA merge: the threads' windows, exactly ----
+  for (int i = warp; i < ACC_DIGITS; i += NW) {
+    int64_t s = 0;
+    for (int j = lane; j < TR_T; j += 32) {
+      const int tp = tops[j];
+      if (tp >= 0 && i <= tp && i > tp - R) s += tr_cols[(i & (R - 1)) * TR_T + j];
+    }
+    s = warp_sum(s);
+    if (lane == 0) blk[i] = s;
+  }
+  __syncthreads();
+  if (t < ACC_WORDS - ACC_DIGITS)
+    blk[ACC_DIGITS + t] = flag_word(ACC_DIGITS + t, blk_flags, blockIdx.x == 0 ? a.n : 0);
+  if (t == 0) {
+    if (blk_events) atomicAdd(&a.state[0], blk_events);
+    if (blk_maxdrop >= 0) atomicMax(&a.state[1], (unsigned long long)(blk_maxdrop + 1));
+  }
+  __syncthreads();
+  if (t < ACC_WORDS) a.partials[blockIdx.x * ACC_WORDS + t] = blk[t];
+  __threadfence();
+  __syncthreads();
+  if (t == 0) is_last = (atomicAdd(a.ticket, 1u) == (unsigned)(G - 1)) ? 1u : 0u;
+  __syncthreads();
+  if (!is_last) return;
+
+  // ---- last CTA: merge the partials, round, stopping condition ----
+  __threadfence();
+  if (t < ACC_WORDS) {
+    int64_t s = 0;
+    for (int64_t r = 0; r < G; ++r) s += __ldcg((const long long*)a.partials + r * ACC_WORDS + t);
+    blk[t] = s;
+  }
+  __syncthreads();
+  if (t == 0) {
+    *a.ticket = 0u;
+    regularise72(blk);
+    const uint64_t y = finalize_acc(blk, limbs, DT, a.out, a.mode);
+    const unsigned long long ev = __ldcg(&a.state[0]);
+    const int md = (int)__ldcg(&a.state[1]) - 1;
+    unsigned long long stop = 1;
+    if (ev > 0 && (md < 0 || md + 1 >= ACC_DIGITS)) stop = 0;  // no usable bound: go on
+    else if (ev > 0) {
+      // B = ev * 2^(32 md + 52) = (ev * 2^20) at digit md + 1
+      const int64_t b = (int64_t)(ev << 20);
+      for (int sgn = -1; sgn <= 1 && stop; sgn += 2) {
+        for (int k = 0; k < ACC_WORDS; ++k) tmp[k] = blk[k];
+        tmp[md + 1] += sgn * b;
+        regularise72(tmp);
+        if (finalize_acc(tmp, limbs, DT, a.out, a.mode) != y) stop = 0;
+      }
+    }
+    store_result(a.result, a.out, y);
+    a.state[2] = stop;
+  }
+}
+
+template <int DT, int R>
+static cudaError_t launch_trunc_t(const TruncArgs& a, int max_ctas, cudaStream_t stream) {
+  constexpr size_t SMEM = (size_t)R * TR_T * sizeof(int64_t);
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    e = cudaFuncSetAttribute(trunc_sum_kernel<DT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  const int64_t want = (a.nvec + 2 * TR_T - 1) / (2 * TR_T);
+  const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
+  trunc_sum_kernel<DT, R><<<grid, TR_T, SMEM, stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <int DT>
+static cudaError_t launch_trunc_dt(int R, const TruncArgs& a, int max_ctas, cudaStream_t stream) {
+  switch (R) {
+    case 2: return launch_trunc_t<DT, 2>(a, max_ctas, stream);
+    case 4: return launch_trunc_t<DT, 4>(a, max_ctas, stream);
+    default: return launch_trunc_t<DT, 16>(a, max_ctas, stream);
+  }
+}
+
+static cudaError_t launch_trunc(int in_dt, int R, const TruncArgs& a, int max_ctas, cudaStream_t stream) {
+  switch (in_dt) {
+    case F64: return launch_trunc_dt<F64>(R, a, max_ctas, stream);
+    case F32: return launch_trunc_dt<F32>(R, a, max_ctas, stream);
+    default: return launch_trunc_dt<BF16>(R, a, max_ctas, stream);
+  }
+}
+
+}  // namespace es
+
+extern "C" exactsum_status exactsum_sum_adaptive(exactsum_t h, const void* d_x, int64_t n, int in_dtype,
+                                                 int out_dtype, int mode, void* d_result, int* passes,
+                                                 int* last_r, exactsum_stream_t stream) {
+  exactsum_status st = es_check_common(h, d_x, n, in_dtype, out_dtype, mode, d_result);
+  if (st != EXACTSUM_OK) return st;
+  if (cudaSetDevice(h->device) != cudaSuccess) return es_cuda_fail(h, cudaGetLastError(), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (!h->trunc_state) {
+    if ((e = cudaMalloc(&h->trunc_state, 64)) != cudaSuccess) return es_cuda_fail(h, e, "cudaMalloc(state)");
+    if ((e = cudaMallocHost(&h->trunc_state_host, 64)) != cudaSuccess)
+      return es_cuda_fail(h, e, "cudaMallocHost(state)");
+  }
+  // digits a format's exact sum can occupy: above this R nothing is truncated
+  const int digits = in_dtype == EXACTSUM_F64 ? 67 : (in_dtype == EXACTSUM_F32 ? 10 : 9);
+  const es::SumArgs base = es_make_sum_args(d_x, n, in_dtype);
+  int pass = 0;
+  for (int R = 2; R < digits && n > 0; R = R * R) {
+    ++pass;
+    es::TruncArgs a;
+    a.x = base.x;
+    a.n = base.n;
+    a.head = base.head;
+    a.nvec = base.nvec;
+    a.tail = base.tail;
+    a.out = out_dtype;
+    a.mode = mode;
+    a.result = d_result;
+    a.partials = h->partials;
+    a.ticket = h->ticket;
+    a.state = h->trunc_state;
+    if ((e = cudaMemsetAsync(h->trunc_state, 0, 64, s)) != cudaSuccess) return es_cuda_fail(h, e, "cudaMemsetAsync");
+    if ((e = es::launch_trunc(in_dtype, R, a, h->max_ctas, s)) != cudaSuccess)
+      return es_cuda_fail(h, e, "truncated sum kernel launch");
+    if ((e = cudaMemcpyAsync(h->trunc_state_host, h->trunc_state, 64, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return es_cuda_fail(h, e, "cudaMemcpyAsync(state)");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return es_cuda_fail(h, e, "cudaStreamSynchronize");
+    if (h->trunc_state_host[2]) {
+      if (passes) *passes = pass;
+      if (last_r) *last_r = R;
+      return EXACTSUM_OK;
+    }
+  }
+  // untruncated: the exact single-pass sum
+  st = exactsum_sum(h, d_x, n, in_dtype, out_dtype, mode, d_result, stream);
+  if (st != EXACTSUM_OK) return st;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return es_cuda_fail(h, e, "cudaStreamSynchronize");
+  if (passes) *passes = pass + 1;
+  if (last_r) *last_r = 0;
+  return EXACTSUM_OK;
+}

@@ -44,6 +44,8 @@ void es_workspace_free(exactsum_t h) {
   cudaFree(h->host_acc);
   cudaFree(h->d_result_tmp);
   if (h->h_result_pinned) cudaFreeHost(h->h_result_pinned);
+  cudaFree(h->trunc_state);
+  if (h->trunc_state_host) cudaFreeHost(h->trunc_state_host);
   es_segment_free_extra(h);
   cudaFree(h->seg_acc);
   cudaFree(h->seg_tile_base);
