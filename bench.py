@@ -605,8 +605,9 @@ def run_ours(args):
     line["context"] = {"naive_fp64_sum": naive_sum_context(torch, x, n, result_bits, stream)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(bits, passes=3, gpu_bits=result_bits)
-    if ws == 1 and args.log2n == LOG2N and not args.primary_only:
+    if ws == 1 and (args.adaptive or (args.log2n == LOG2N and not args.primary_only)):
         line["adaptive"] = bench_adaptive(es, torch, dev, x, n)
+    if ws == 1 and args.log2n == LOG2N and not args.primary_only:
         del x
         torch.cuda.empty_cache()
         line["segmented"] = bench_segmented(es, W, torch, dev, args.steps, args.segments,
@@ -637,6 +638,8 @@ def main():
                     help="print the exponent-range sweep over the four dataset families instead")
     ap.add_argument("--requests", type=int, default=100_000,
                     help="requests of the serving measurement (0 skips it)")
+    ap.add_argument("--adaptive", action="store_true",
+                    help="also time the condition-number-sensitive path with --primary-only or --log2n")
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64",
                     help="f32/bf16: profiling line for the narrow formats instead of the benchmark")
     ap.add_argument("--log2n", type=int, default=None,

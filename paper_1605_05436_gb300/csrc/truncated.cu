@@ -49,7 +49,10 @@ struct TruncArgs {
 };
 
 constexpr int TR_T = 512;  // threads per CTA
-constexpr int TR_U = 4;    // 16-byte vectors per thread per batch
+#ifndef ES_TR_U
+#define ES_TR_U 2
+#endif
+constexpr int TR_U = ES_TR_U;  // 16-byte vectors per thread per batch (two batches in flight)
 constexpr int TR_REG_EVERY = 1984;  // digit parts between window regularisations (each < 2^52)
 
 // An element as two radix-2^32 digit parts: value = lo * 2^(32k) + hi * 2^(32(k+1))
@@ -91,6 +94,67 @@ __device__ __forceinline__ void split32(uint64_t bits, int& k, int64_t& lo, int6
 
 // The R-digit window of one thread: digit i (top - R < i <= top) lives in
 // slot i mod R of the thread's column (slot s at col[s * TR_T]).
+//
+// The rare window moves are kept out of line (so that the per-element path
+// stays small) and report what they did packed into one 64-bit value:
+// new top | (items dropped) << 16 | (highest dropped digit + 1) << 32.
+template <int R>
+__device__ __forceinline__ int64_t& win_slot(int64_t* col, int i) {
+  return col[(i & (R - 1)) * TR_T];
+}
+
+__device__ __forceinline__ uint64_t win_pack(int top, uint32_t dropped, int maxdrop) {
+  return (uint64_t)(uint32_t)top | ((uint64_t)dropped << 16) | ((uint64_t)(uint32_t)(maxdrop + 1) << 32);
+}
+
+// Lemma 1 carries inside the window (balanced digits); a carry out of the
+// top digit moves the window up by one.
+template <int R>
+__device__ __noinline__ uint64_t win_regularise(int64_t* col, int top) {
+  uint32_t dropped = 0;
+  int maxdrop = -1;
+  int64_t carry = 0;
+  for (int i = top - R + 1; i <= top; ++i) {
+    const int64_t v = win_slot<R>(col, i) + carry;
+    const int64_t c = (v + ((int64_t)1 << 31)) >> 32;
+    win_slot<R>(col, i) = v - (c << 32);
+    carry = c;
+  }
+  if (carry != 0) {
+    int64_t& s = win_slot<R>(col, top + 1);  // holds digit top + 1 - R, now leaving the window
+    if (s != 0) {
+      ++dropped;
+      maxdrop = top + 1 - R;
+    }
+    s = carry;
+    ++top;
+  }
+  return win_pack(top, dropped, maxdrop);
+}
+
+// Move the window up so that its top digit is t (> top), regularising first.
+template <int R>
+__device__ __noinline__ uint64_t win_raise(int64_t* col, int top, int t) {
+  const uint64_t rg = win_regularise<R>(col, top);
+  top = (int)(rg & 0xFFFF);
+  uint32_t dropped = (uint32_t)((rg >> 16) & 0xFFFF);
+  int maxdrop = (int)(rg >> 32) - 1;
+  if (t > top) {
+    const int lo = t - top >= R ? top - R + 1 : top + 1 - R;
+    const int hi = t - top >= R ? top : t - R;
+    for (int i = lo; i <= hi; ++i) {  // digits leaving the window
+      int64_t& s = win_slot<R>(col, i);
+      if (s != 0) {
+        ++dropped;
+        maxdrop = max(maxdrop, i);
+        s = 0;
+      }
+    }
+    top = t;
+  }
+  return win_pack(top, dropped, maxdrop);
+}
+
 template <int R>
 struct Window {
   int64_t* col;
@@ -99,71 +163,44 @@ struct Window {
   int maxdrop;                 // highest digit index dropped; -1 if none
   int adds;                    // parts added since the last regularisation
 
-  __device__ __forceinline__ int64_t& slot(int i) { return col[(i & (R - 1)) * TR_T]; }
-
-  __device__ __forceinline__ void drop(int j) {
-    ++events;
-    maxdrop = max(maxdrop, j);
+  __device__ __forceinline__ void absorb(uint64_t r) {
+    top = (int)(r & 0xFFFF);
+    events += (r >> 16) & 0xFFFF;
+    maxdrop = max(maxdrop, (int)(r >> 32) - 1);
   }
 
-  // Lemma 1 carries inside the window (balanced digits); a carry out of the
-  // top digit moves the window up by one.
-  __device__ void regularise() {
+  __device__ __forceinline__ void regularise() {
     adds = 0;
-    if (top < 0) return;
-    int64_t carry = 0;
-#pragma unroll
-    for (int i = top - R + 1; i <= top; ++i) {
-      const int64_t v = slot(i) + carry;
-      const int64_t c = (v + ((int64_t)1 << 31)) >> 32;
-      slot(i) = v - (c << 32);
-      carry = c;
-    }
-    if (carry != 0) {
-      int64_t& s = slot(top + 1);  // holds digit top + 1 - R, now leaving the window
-      if (s != 0) drop(top + 1 - R);
-      s = carry;
-      ++top;
-    }
+    if (top >= 0) absorb(win_regularise<R>(col, top));
   }
 
-  // Move the window up so that its top digit is t (> top).
-  __device__ void raise(int t) {
-    regularise();
-    if (t <= top) return;
-    if (t - top >= R) {
-#pragma unroll
-      for (int i = top - R + 1; i <= top; ++i)
-        if (slot(i) != 0) {
-          drop(i);
-          slot(i) = 0;
-        }
-    } else {
-      for (int i = top + 1; i <= t; ++i) {
-        int64_t& s = slot(i);  // holds digit i - R
-        if (s != 0) {
-          drop(i - R);
-          s = 0;
-        }
-      }
+  // Add an element's parts: lo at digit k, hi at digit k + 1.  The window
+  // moves up only for a non-zero part above it; adding a zero part to any
+  // slot changes nothing, so only non-zero parts below the window count as
+  // dropped.
+  __device__ __forceinline__ void add_pair(int k, int64_t lo, int64_t hi) {
+    const int t = hi != 0 ? k + 1 : k;
+    if (top < 0) {
+      top = t;
+    } else if (t > top) {
+      absorb(win_raise<R>(col, top, t));
+      adds = 0;
     }
-    top = t;
-  }
-
-  __device__ __forceinline__ void add(int j, int64_t v) {
-    if (v == 0) return;
-    if (top < 0) top = j;
-    else if (j > top) raise(j);
-    if (j <= top - R) {
-      drop(j);
-      return;
+    const int low = top - R;  // digits <= low are outside the window
+    if (k + 1 > low) {
+      win_slot<R>(col, k + 1) += hi;
+    } else if (hi != 0) {
+      ++events;
+      maxdrop = max(maxdrop, k + 1);
     }
-    slot(j) += v;
-    if (++adds >= TR_REG_EVERY) regularise();
-  }
-
-  __device__ __forceinline__ int64_t digit(int i) const {
-    return (top >= 0 && i <= top && i > top - R) ? col[(i & (R - 1)) * TR_T] : 0;
+    if (k > low) {
+      win_slot<R>(col, k) += lo;
+    } else if (lo != 0) {
+      ++events;
+      maxdrop = max(maxdrop, k);
+    }
+    adds += 2;
+    if (adds >= TR_REG_EVERY) regularise();
   }
 };
 
@@ -175,8 +212,7 @@ __device__ __forceinline__ void add_elem(Window<R>& w, uint64_t bits, uint32_t& 
   int k;
   int64_t lo, hi;
   split32<DT>(bits, k, lo, hi);
-  w.add(k + 1, hi);
-  w.add(k, lo);
+  w.add_pair(k, lo, hi);
 }
 
 template <int DT, int R>
@@ -236,12 +272,26 @@ __global__ void __launch_bounds__(TR_T, 1) trunc_sum_kernel(TruncArgs a) {
   const int64_t cnt = (vb + t < ve) ? (ve - vb - t + TR_T - 1) / TR_T : 0;
   const uint4* p = vx + vb + t;
   const int64_t nb = cnt / TR_U;
-  uint4 A[TR_U];
-  for (int64_t k = 0; k < nb; ++k) {
+  // two batches in flight: the next batch loads while this one is added
+  uint4 A[TR_U], B[TR_U];
+  if (nb > 0) {
 #pragma unroll
-    for (int u = 0; u < TR_U; ++u) A[u] = ldg_stream(p + (k * TR_U + u) * TR_T);
+    for (int u = 0; u < TR_U; ++u) A[u] = ldg_stream(p + u * TR_T);
+  }
+  for (int64_t k = 0; k < nb; k += 2) {
+    if (k + 1 < nb) {
+#pragma unroll
+      for (int u = 0; u < TR_U; ++u) B[u] = ldg_stream(p + ((k + 1) * TR_U + u) * TR_T);
+    }
 #pragma unroll
     for (int u = 0; u < TR_U; ++u) add_vec16<DT, R>(w, A[u], emax);
+    if (k + 1 >= nb) break;
+    if (k + 2 < nb) {
+#pragma unroll
+      for (int u = 0; u < TR_U; ++u) A[u] = ldg_stream(p + ((k + 2) * TR_U + u) * TR_T);
+    }
+#pragma unroll
+    for (int u = 0; u < TR_U; ++u) add_vec16<DT, R>(w, B[u], emax);
   }
   for (int64_t j = nb * TR_U; j < cnt; ++j) add_vec16<DT, R>(w, ldg_stream(p + j * TR_T), emax);
   if (blockIdx.x == 0 && t < a.head) add_elem<DT, R>(w, load_one<DT>(a.x, t), emax);
