@@ -591,6 +591,7 @@ def run_ours(args):
                    "launch": "exactsum_sum, one kernel per step"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "frac_of_nominal_8000_gbs": round(achieved / 8000.0, 4),
                      "peak_kind": f"{peak_kind} (STREAM-style copy)",
                      "kernel": "es::sum_kernel_tma<F64, 8 consumer warps, 11 vectors per thread per stage, 2 stages>",
                      "algorithmic_bytes_per_launch": n * BYTES_PER_ELEM,
