@@ -593,7 +593,7 @@ def run_ours(args):
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "frac_of_nominal_8000_gbs": round(achieved / 8000.0, 4),
                      "peak_kind": f"{peak_kind} (STREAM-style copy)",
-                     "kernel": "es::sum_kernel_tma<F64, 8 consumer warps, 11 vectors per thread per stage, 2 stages>",
+                     "kernel": "es::sum_kernel_tma<F64, 8 consumer warps, 10 vectors per thread per stage, 2 stages>",
                      "algorithmic_bytes_per_launch": n * BYTES_PER_ELEM,
                      "avg_kernel_ms": round(avg_kernel_ms, 4)},
         "e2e": e2e,
@@ -605,7 +605,7 @@ def run_ours(args):
         line["config"]["workload"] = f"profiling case: n = 2^{args.log2n}, same recipe"
     line["context"] = {"naive_fp64_sum": naive_sum_context(torch, x, n, result_bits, stream)}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(bits, passes=3, gpu_bits=result_bits)
+        line["cpu_baseline"] = cpu_baseline(bits, passes=8, gpu_bits=result_bits)
     if ws == 1 and (args.adaptive or (args.log2n == LOG2N and not args.primary_only)):
         line["adaptive"] = bench_adaptive(es, torch, dev, x, n)
     if ws == 1 and args.log2n == LOG2N and not args.primary_only:

@@ -433,6 +433,78 @@ __device__ __forceinline__ int64_t digit32(const uint32_t* __restrict__ col, int
   return v;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 with radix-2^16 sign-split columns (uint64_t digits): 18 digits per
+// half cover the 277-bit range, so the two halves (positive and negative
+// elements) take 288 B per thread; an element adds m << (p & 15) (< 2^39,
+// a 64-bit shift) into digit (p >> 4) of its half, with no sign arithmetic.
+// ---------------------------------------------------------------------------
+constexpr int F32_R16_DIGITS = 18;
+template <>
+struct ColumnDigits<F32, uint64_t> {
+  static constexpr int value = 2 * F32_R16_DIGITS;
+};
+
+template <int STRIDE>
+__device__ __forceinline__ void add_f32_r16(uint64_t* __restrict__ col, uint32_t w, uint32_t E) {
+  const uint32_t m = (w & 0x7FFFFFu) | (E != 0u ? 0x800000u : 0u);
+  const uint32_t p = max(E, 1u) - 1u;
+  col[((p >> 4) + (w >> 31) * (uint32_t)F32_R16_DIGITS) * STRIDE] += (uint64_t)m << (p & 15u);
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_vec(uint64_t* __restrict__ col, const uint4& v, uint32_t& emax) {
+  static_assert(DT == F32, "radix-2^16 split columns hold FP32 sums only");
+  const uint32_t e0 = (v.x >> 23) & 0xFFu, e1 = (v.y >> 23) & 0xFFu;
+  const uint32_t e2 = (v.z >> 23) & 0xFFu, e3 = (v.w >> 23) & 0xFFu;
+  emax = __vimax3_u32(__vimax3_u32(emax, e0, e1), e2, e3);
+  add_f32_r16<STRIDE>(col, v.x, e0);
+  add_f32_r16<STRIDE>(col, v.y, e1);
+  add_f32_r16<STRIDE>(col, v.z, e2);
+  add_f32_r16<STRIDE>(col, v.w, e3);
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_one(uint64_t* __restrict__ col, uint64_t bits, uint32_t& emax) {
+  static_assert(DT == F32, "radix-2^16 split columns hold FP32 sums only");
+  const uint32_t w = (uint32_t)bits;
+  const uint32_t E = (w >> 23) & 0xFFu;
+  emax = max(emax, E);
+  add_f32_r16<STRIDE>(col, w, E);
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void regularise(uint64_t* __restrict__ col) {
+  static_assert(DT == F32, "radix-2^16 split columns hold FP32 sums only");
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint64_t* c = col + h * F32_R16_DIGITS * STRIDE;
+    uint64_t carry = 0;
+#pragma unroll 3
+    for (int i = 0; i < F32_R16_DIGITS - 1; ++i) {
+      const uint64_t v = c[i * STRIDE] + carry;
+      c[i * STRIDE] = v & 0xFFFFu;
+      carry = v >> 16;
+    }
+    c[(F32_R16_DIGITS - 1) * STRIDE] += carry;
+  }
+}
+
+// radix-2^32 digit i = radix-2^16 digits 2i and 2i + 1, positive half minus
+// negative half
+template <int DT, int STRIDE>
+__device__ __forceinline__ int64_t digit32(const uint64_t* __restrict__ col, int i) {
+  static_assert(DT == F32, "radix-2^16 split columns hold FP32 sums only");
+  int64_t v = 0;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int j = 2 * i + k;
+    if (j < F32_R16_DIGITS)
+      v += ((int64_t)col[j * STRIDE] - (int64_t)col[(F32_R16_DIGITS + j) * STRIDE]) * ((int64_t)1 << (16 * k));
+  }
+  return v;
+}
+
 // Additions between regularisations for a digit type.
 template <int DT, typename D>
 struct RegEvery {
@@ -445,6 +517,10 @@ struct RegEvery<BF16, int32_t> {
 template <>
 struct RegEvery<BF16, uint32_t> {
   static constexpr int value = 120000;  // 255 + 120,000 * 2^15 < 2^32
+};
+template <>
+struct RegEvery<F32, uint64_t> {
+  static constexpr int value = 1 << 24;  // 2^16 + 2^24 * 2^39 < 2^64
 };
 
 // Classify one element for the special-value and signed-zero counters.

@@ -283,9 +283,10 @@ struct SumConfig;
 // Streaming form and shape per input format (chosen by measurement):
 //   TMA = 1: sum_kernel_tma<DT, C, TU, S>, (C + 1) warps, S stages of C*32*TU vectors;
 //   TMA = 0: sum_kernel<DT, T, U>, T threads, U vectors per batch.
-// Digit columns: int64 for FP64 and FP32; for BF16 sign-split unsigned
-// 32-bit halves (ES_BF16_SPLIT = 1), else signed int32 (ES_BF16_I32 = 1) or
-// int64.
+// Digit columns: int64 for FP64; for FP32 radix-2^16 sign-split unsigned
+// 64-bit halves (ES_F32_R16 = 1; else radix-2^8 int64); for BF16 sign-split
+// unsigned 32-bit halves (ES_BF16_SPLIT = 1), else signed int32
+// (ES_BF16_I32 = 1) or int64.
 #ifndef ES_F64_TMA
 #define ES_F64_TMA 1
 #endif
@@ -293,7 +294,7 @@ struct SumConfig;
 #define ES_F64_C 8
 #endif
 #ifndef ES_F64_TU
-#define ES_F64_TU 11
+#define ES_F64_TU 10
 #endif
 #ifndef ES_F64_S
 #define ES_F64_S 2
@@ -317,7 +318,7 @@ struct SumConfig;
 #define ES_F32_S 4
 #endif
 #ifndef ES_F32_T
-#define ES_F32_T 512
+#define ES_F32_T 768
 #endif
 #ifndef ES_F32_U
 #define ES_F32_U 4
@@ -350,9 +351,16 @@ template <> struct SumConfig<F64> {
   static constexpr int TMA = ES_F64_TMA, C = ES_F64_C, TU = ES_F64_TU, S = ES_F64_S, T = ES_F64_T, U = ES_F64_U;
   using Digit = int64_t;
 };
+#ifndef ES_F32_R16
+#define ES_F32_R16 1
+#endif
 template <> struct SumConfig<F32> {
   static constexpr int TMA = ES_F32_TMA, C = ES_F32_C, TU = ES_F32_TU, S = ES_F32_S, T = ES_F32_T, U = ES_F32_U;
+#if ES_F32_R16
+  using Digit = uint64_t;
+#else
   using Digit = int64_t;
+#endif
 };
 template <> struct SumConfig<BF16> {
   static constexpr int TMA = ES_BF16_TMA, C = ES_BF16_C, TU = ES_BF16_TU, S = ES_BF16_S, T = ES_BF16_T,
