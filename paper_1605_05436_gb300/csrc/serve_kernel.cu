@@ -22,7 +22,10 @@ namespace es {
 
 constexpr int SERVE_W = SERVE_WARPS_PER_CTA;
 constexpr int SERVE_T = SERVE_W * 32;
-constexpr int SERVE_U = 4;
+#ifndef ES_SERVE_U
+#define ES_SERVE_U 6
+#endif
+constexpr int SERVE_U = ES_SERVE_U;
 constexpr int SERVE_ND = Geometry<F64>::DIGITS;  // column height (FP64 is the tallest)
 
 template <int DT>
