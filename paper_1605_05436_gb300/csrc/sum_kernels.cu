@@ -336,7 +336,7 @@ struct SumConfig;
 #define ES_BF16_S 4
 #endif
 #ifndef ES_BF16_T
-#define ES_BF16_T 512
+#define ES_BF16_T 768
 #endif
 #ifndef ES_BF16_U
 #define ES_BF16_U 4
