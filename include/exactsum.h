@@ -201,6 +201,24 @@ exactsum_status exactsum_acc_round(exactsum_t h, const void* d_acc, int in_dtype
 #define EXACTSUM_STATUS_MAP_OVERFLOW 2 /* more tiles than the tile map holds (input larger than HBM) */
 #define EXACTSUM_STATUS_TIMEOUT 4      /* a bounded wait inside a kernel gave up; that result is invalid */
 
+/* Diagnostic of the bounded waits (no paper counterpart).  Every wait
+ * inside this library's kernels polls its mbarrier a bounded number of
+ * times; if the phase has not completed by then the kernel sets
+ * EXACTSUM_STATUS_TIMEOUT in the handle's device status word, waits
+ * (bounded) for its own copies in flight and returns, so that the CUDA
+ * context stays usable and the host learns of the failure from
+ * exactsum_device_status.  This call runs that path on purpose: one thread
+ * waits on an mbarrier that nothing ever completes, polling it `polls`
+ * times (0: the kernels' own limit, through their own wait function), then
+ * records EXACTSUM_STATUS_TIMEOUT.
+ *   d_elapsed_ns: one uint64 in device memory (8-byte aligned) that receives
+ *     the wait's duration in nanoseconds, or NULL.
+ * Asynchronous on `stream`.  Errors: EXACTSUM_EINVAL for a null handle or a
+ * misaligned d_elapsed_ns (nothing enqueued); EXACTSUM_ECUDA for a failed
+ * launch. */
+exactsum_status exactsum_check_timeout(exactsum_t h, uint32_t polls, uint64_t* d_elapsed_ns,
+                                       exactsum_stream_t stream);
+
 /* d_results[s] <- round(sum of d_x[d_offsets[s] .. d_offsets[s+1])) for
  * s in [0, num_segments).
  *   d_offsets: num_segments + 1 int64 CSR offsets in device memory (any

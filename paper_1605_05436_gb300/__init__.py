@@ -61,6 +61,7 @@ _SIGNATURES = {
     "exactsum_server_stats": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "exactsum_server_destroy": [_vp],
     "exactsum_segmented_sum_noalloc": [_vp, _vp, _i64, _int, _int, _int, _vp, _vp],
+    "exactsum_check_timeout": [_vp, ctypes.c_uint32, _vp, _vp],
 }
 OPTIONAL_SIGNATURES: dict = {}
 
@@ -204,7 +205,13 @@ def exactsum_device_status(handle) -> int:
     return v.value
 
 
-STATUS_BAD_OFFSETS, STATUS_MAP_OVERFLOW = 1, 2
+STATUS_BAD_OFFSETS, STATUS_MAP_OVERFLOW, STATUS_TIMEOUT = 1, 2, 4
+
+
+def exactsum_check_timeout(handle, polls, d_elapsed_ns, stream) -> None:
+    """Run one bounded wait that is never satisfied (the kernels' timeout
+    path); afterwards exactsum_device_status reports STATUS_TIMEOUT."""
+    _check(library().exactsum_check_timeout(handle, polls, d_elapsed_ns, stream), handle)
 NOALLOC_MAX_SEGMENTS = 2048
 
 

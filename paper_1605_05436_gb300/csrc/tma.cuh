@@ -9,7 +9,10 @@
 
 namespace es {
 
-constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 24;
+// An unsatisfied try_wait suspends the polling thread for about 3.75 us on
+// GB300 (measured through exactsum_check_timeout), so 2^18 polls give up
+// after about one second; a copy or a stage release takes microseconds.
+constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 18;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
