@@ -478,16 +478,35 @@ __device__ __forceinline__ void add_f32_r16(uint64_t* __restrict__ col, uint32_t
   col[((p >> 4) + (w >> 31) * (uint32_t)F32_R16_DIGITS) * STRIDE] += (uint64_t)m << (p & 15u);
 }
 
+// Two FP32 elements decoded together in 16-bit halves: one byte permute
+// brings both exponents (and both signs) into one word, then p = max(E - 1, 0)
+// is one add-max of 16-bit pairs, the hidden bits one 16-bit-pair minimum,
+// the digit index (half offset included) one add of pairs.  The running
+// exponent maximum is kept as two 16-bit maxima packed in one word
+// (emax_unpack gives the plain maximum).  (Measured 3.6% faster than
+// decoding each element on its own; the same pairing measured 4% slower for
+// FP64, whose 11-bit exponents and two-digit additions leave less to share.)
+template <int STRIDE>
+__device__ __forceinline__ void add_f32_r16_pair(uint64_t* __restrict__ col, uint32_t w0, uint32_t w1,
+                                                 uint32_t& emax2) {
+  const uint32_t hh = __byte_perm(w0, w1, 0x7632);      // (w0 >> 16) | (w1 & 0xFFFF0000)
+  const uint32_t E2 = (hh >> 7) & 0x00FF00FFu;          // E of w0 in bits 0-7, of w1 in bits 16-23
+  emax2 = __vimax3_u16x2(emax2, E2, E2);
+  const uint32_t p2 = __viaddmax_s16x2(E2, 0xFFFFFFFFu, 0u);       // max(E - 1, 0) per half
+  const uint32_t hb2 = __vimin3_u16x2(E2, 0x00010001u, 0x00010001u);  // E >= 1 per half
+  // digit p >> 4 of the element's half (negative elements: + F32_R16_DIGITS)
+  const uint32_t q2 = ((p2 >> 4) & 0x000F000Fu) + ((hh >> 15) & 0x00010001u) * (uint32_t)F32_R16_DIGITS;
+  const uint32_t m0 = (w0 & 0x7FFFFFu) | (hb2 << 23);
+  const uint32_t m1 = (w1 & 0x7FFFFFu) | ((hb2 << 7) & 0x800000u);
+  col[(q2 & 0xFFFFu) * STRIDE] += (uint64_t)m0 << (p2 & 15u);
+  col[(q2 >> 16) * STRIDE] += (uint64_t)m1 << ((p2 >> 16) & 15u);
+}
+
 template <int DT, int STRIDE>
 __device__ __forceinline__ void add_vec(uint64_t* __restrict__ col, const uint4& v, uint32_t& emax) {
   static_assert(DT == F32, "radix-2^16 split columns hold FP32 sums only");
-  const uint32_t e0 = (v.x >> 23) & 0xFFu, e1 = (v.y >> 23) & 0xFFu;
-  const uint32_t e2 = (v.z >> 23) & 0xFFu, e3 = (v.w >> 23) & 0xFFu;
-  emax = __vimax3_u32(__vimax3_u32(emax, e0, e1), e2, e3);
-  add_f32_r16<STRIDE>(col, v.x, e0);
-  add_f32_r16<STRIDE>(col, v.y, e1);
-  add_f32_r16<STRIDE>(col, v.z, e2);
-  add_f32_r16<STRIDE>(col, v.w, e3);
+  add_f32_r16_pair<STRIDE>(col, v.x, v.y, emax);
+  add_f32_r16_pair<STRIDE>(col, v.z, v.w, emax);
 }
 
 template <int DT, int STRIDE>
@@ -529,6 +548,14 @@ __device__ __forceinline__ int64_t digit32(const uint64_t* __restrict__ col, int
       v += ((int64_t)col[j * STRIDE] - (int64_t)col[(F32_R16_DIGITS + j) * STRIDE]) * ((int64_t)1 << (16 * k));
   }
   return v;
+}
+
+// The exponent maximum as add_vec leaves it: one value, or for the FP32
+// radix-2^16 columns two 16-bit maxima packed in one word.
+template <int DT, typename D>
+__device__ __forceinline__ uint32_t emax_unpack(uint32_t e) {
+  if constexpr (DT == F32 && sizeof(D) == 8 && D(-1) > D(0)) return max(e & 0xFFFFu, e >> 16);
+  else return e;
 }
 
 // Additions between regularisations for a digit type.

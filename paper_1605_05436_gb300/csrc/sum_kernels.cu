@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   // ---- hot loop: this thread's vectors vb + t + j*T, double buffered ----
   const int64_t cnt = (vb + t < ve) ? (ve - vb - t + T - 1) / T : 0;
   stream_add<DT, T, T, U>(col, vx + vb + t, cnt, emax, reg_left, t, vx + ve);
+  emax = emax_unpack<DT, D>(emax);
 
   // ---- unaligned head (CTA 0) and ragged tail (last CTA) ----
   if (blockIdx.x == 0 && t < a.head) add_one<DT, T>(col, load_one<DT>(a.x, t), emax);
@@ -318,10 +319,10 @@ struct SumConfig;
 #define ES_F32_S 4
 #endif
 #ifndef ES_F32_T
-#define ES_F32_T 768
+#define ES_F32_T 640
 #endif
 #ifndef ES_F32_U
-#define ES_F32_U 4
+#define ES_F32_U 5
 #endif
 #ifndef ES_BF16_TMA
 #define ES_BF16_TMA 0
