@@ -183,6 +183,22 @@ def cpu_baseline(bits, passes: int, gpu_bits=None):
     return out
 
 
+# The paper's own measurements (Section 6.3), for context only: relative
+# numbers from a CPU MapReduce (Spark) implementation; the paper prints no
+# absolute times and no GPU figures, so there is no number to divide by.
+PAPER_CONTEXT = {
+    "source": "Goodrich & Eldawy, arXiv:1605.05436, Section 6.3 (experiments)",
+    "hardware": "one AWS r3.8xlarge: 32 cores (Intel Xeon E5-2670 v2), 244 GB RAM; Spark 1.6.0 with 32 "
+                "local workers on OpenJDK 1.7; baseline iFastSum in C++ (gcc 4.8.4)",
+    "workload": "FP64, 1e6 to 1e9 numbers, exponent range delta = 2000 (10 to 2000 in a sweep), disk I/O not counted",
+    "reported": "MapReduce with sparse or small superaccumulators up to 80x faster than sequential "
+                "iFastSum; iFastSum faster below about 1e7 numbers; small accumulator slightly faster "
+                "than sparse; linear scaling with cores up to 16, saturating from 16 to 32 (hyper-threads)",
+    "absolute_times": None,
+    "role": "context, not a target",
+}
+
+
 def naive_sum_context(torch, x, n, exact_bits, stream):
     """Context only: the plain FP64 tree reduction (torch.sum) on the same
     device array, its time and its error against the exact sum, in units in
@@ -603,7 +619,8 @@ def run_ours(args):
     }
     if args.log2n != LOG2N:
         line["config"]["workload"] = f"profiling case: n = 2^{args.log2n}, same recipe"
-    line["context"] = {"naive_fp64_sum": naive_sum_context(torch, x, n, result_bits, stream)}
+    line["context"] = {"naive_fp64_sum": naive_sum_context(torch, x, n, result_bits, stream),
+                       "paper": PAPER_CONTEXT}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(bits, passes=8, gpu_bits=result_bits)
     if ws == 1 and (args.adaptive or (args.log2n == LOG2N and not args.primary_only)):
