@@ -77,3 +77,16 @@ def test_check_timeout_argument_errors():
         assert es.exactsum_device_status(h) == 0  # nothing was enqueued
     finally:
         es.exactsum_destroy(h)
+
+
+def test_the_kernels_own_limit_gives_up_in_about_a_second():
+    # polls = 0 runs the kernels' own wait function with its own limit
+    h = es.exactsum_create(0)
+    try:
+        elapsed = torch.zeros(1, dtype=torch.int64, device=DEV)
+        es.exactsum_check_timeout(h, 0, elapsed.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        assert es.exactsum_device_status(h) == es.STATUS_TIMEOUT
+        seconds = int(elapsed.item()) * 1e-9
+        assert 0.05 < seconds < 10.0, seconds
+    finally:
+        es.exactsum_destroy(h)
