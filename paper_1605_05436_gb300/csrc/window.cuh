@@ -151,10 +151,13 @@ __device__ __forceinline__ void win_tile(const void* x, int64_t elo, int64_t ehi
   uint32_t emax = 0;
   int reg_left = REG_EVERY;
   uint32_t nover = 0;  // this lane's overflow adds since the last check
-  auto add_bits = [&](uint64_t bits) {
+  // one element into the window column or, exactly, into the overflow
+  // accumulator; `track` updates the exponent maximum (the FP64 vector path
+  // does that once per vector with a three-input maximum instead)
+  auto add_bits_e = [&](uint64_t bits, bool track) {
     int d; int64_t lo, hi; uint32_t E;
     decode(bits, d, lo, hi, E);
-    emax = max(emax, E);
+    if (track) emax = max(emax, E);
     const unsigned rel = (unsigned)(d - b);
     if (rel <= (unsigned)(DT == F64 ? WD - 2 : WD - 1)) {
       col[rel * T] += lo;
@@ -165,10 +168,12 @@ __device__ __forceinline__ void win_tile(const void* x, int64_t elo, int64_t ehi
       ++nover;
     }
   };
+  auto add_bits = [&](uint64_t bits) { add_bits_e(bits, true); };
   auto add_vec_w = [&](const uint4& v) {
     if constexpr (DT == F64) {
-      add_bits(((uint64_t)v.y << 32) | v.x);
-      add_bits(((uint64_t)v.w << 32) | v.z);
+      emax = __vimax3_u32(emax, (v.y >> 20) & 0x7FFu, (v.w >> 20) & 0x7FFu);
+      add_bits_e(((uint64_t)v.y << 32) | v.x, false);
+      add_bits_e(((uint64_t)v.w << 32) | v.z, false);
     } else if constexpr (DT == F32) {
       add_bits(v.x); add_bits(v.y); add_bits(v.z); add_bits(v.w);
     } else {
