@@ -269,3 +269,47 @@ def test_invalid_arguments():
     es.exactsum_sum(h, x.data_ptr(), 16, es.F64, es.F64, es.RNE, out.data_ptr(), s)
     torch.cuda.synchronize()
     assert out.item() == 16.0
+
+
+NARROW_SPECIALS = {es.F32: {"nan": 0x7FC00001, "pinf": 0x7F800000, "ninf": 0xFF800000, "negzero": 0x80000000},
+                   es.BF16: {"nan": 0x7FC1, "pinf": 0x7F80, "ninf": 0xFF80, "negzero": 0x8000}}
+
+
+@pytest.mark.parametrize("dt", [es.F32, es.BF16])
+def test_narrow_specials_anywhere(dt):
+    """FP32/BF16 arrays long enough for the vector path (whose kernels decode
+    two elements at once and keep the exponent maximum packed in 16-bit
+    halves): NaN / infinities at even and odd positions (both halves of a
+    decoded pair), alone and together."""
+    rng = np.random.default_rng(31 + dt)
+    n = 300_001
+    base = W.uniform_f32(n, 9) if dt == es.F32 else W.wide_bf16(n, 9)
+    sp = NARROW_SPECIALS[dt]
+    for combo in (["nan"], ["pinf"], ["ninf"], ["pinf", "ninf"], ["ninf", "ninf"]):
+        for where in (0, 1, n // 2, n // 2 + 1, n - 1, int(rng.integers(n))):
+            bits = base.copy()
+            for k, s in enumerate(combo):
+                bits[(where + 7919 * k) % n] = sp[s]
+            for o in (es.F64, dt):
+                assert gpu_sum(bits, dt, o, es.RNE) == oracle.exact_sum(bits, dt, o, es.RNE, 8), (combo, where, o)
+
+
+@pytest.mark.parametrize("dt", [es.F32, es.BF16])
+def test_narrow_signed_zero_rules(dt):
+    """All-zero FP32/BF16 arrays (every exponent maximum 0) take the exact
+    classification: -0 only, +0 only, mixed, and cancelling subnormals."""
+    neg = NARROW_SPECIALS[dt]["negzero"]
+    ut = G.NP_UNSIGNED[dt]
+    for n in (9, 1000, 200_003):
+        for pattern in ("negzero", "poszero", "mixed", "subnormal_cancel"):
+            if pattern == "negzero":
+                bits = np.full(n, neg, dtype=ut)
+            elif pattern == "poszero":
+                bits = np.zeros(n, dtype=ut)
+            elif pattern == "mixed":
+                bits = np.where(np.arange(n) % 3 == 0, ut(neg), ut(0)).astype(ut)
+            else:
+                v = (np.arange(1, n // 2 + 2) % 100 + 1).astype(ut)  # subnormals
+                bits = np.concatenate([v, v ^ ut(neg)])
+            for m in MODES:
+                assert gpu_sum(bits, dt, dt, m) == oracle.exact_sum(bits, dt, dt, m, 4), (n, pattern, m)
