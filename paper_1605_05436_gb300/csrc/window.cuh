@@ -1,18 +1,19 @@
 // window.cuh -- the windowed tile reduction: one warp sums a contiguous
 // range of elements exactly, keeping per lane only a small window of digits
-// plus a warp-shared full-width overflow accumulator.  Used by the segmented
-// windowed reducer and by the serving step.
+// plus a warp-shared full-width overflow accumulator.  The segmented sum's
+// windowed reducer (segmented.cu) runs it over its tile queue.
 //
-// Within one tile the exponents of real data are often concentrated (the
-// paper observes that subtracting the mean leaves a range of about 15
-// exponents), so each lane keeps only WinGeom<DT>::WD digits below the
-// largest digit of the tile's first batch (plus one carry digit), and any
-// element that falls outside the window goes, exactly, into the warp's
-// overflow accumulator in the format's native radix (shared-memory integer
-// atomics).  The small columns let many more warps share an SM than the full
-// 66-digit columns do.  Exact for every input; fast when most elements land
-// in the window (Section 2: a sparse superaccumulator keeps only its active
-// range of indices; here the inactive ones are not dropped, only slower).
+// Within one tile the exponents of real data are often concentrated
+// (Section 6.3 notes that subtracting the mean leaves about 15 exponents in
+// its Anderson-style dataset), so each lane keeps only WinGeom<DT>::WD
+// digits below the largest digit of the tile's first batch (plus one carry
+// digit), and any element that falls outside the window goes, exactly, into
+// the warp's overflow accumulator in the format's native radix
+// (shared-memory integer atomics).  The small columns let many more warps
+// share an SM than the full 66-digit columns do.  Exact for every input;
+// fast when most elements land in the window (Section 2: a sparse
+// superaccumulator keeps only its active range of indices; here the
+// inactive ones are not dropped, only slower).
 #pragma once
 #include <cstdint>
 
