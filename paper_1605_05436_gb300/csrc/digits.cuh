@@ -20,6 +20,11 @@
 //   FP32:   r = 8.   m < 2^24, so m * 2^(p & 7) < 2^31 goes into one digit
 //   BF16:            (p >> 3) without splitting.  33 digits per thread.
 //
+// The single-array FP32 and BF16 kernels use sign-split unsigned columns
+// instead (positive and negative elements in separate halves, so an element
+// needs no sign arithmetic): FP32 radix 2^16 in 64-bit digits, BF16 radix
+// 2^8 in 32-bit digits, each defined below with its decode.
+//
 // Regularisation (Lemma 1, generalised to deferred carries): a digit D is
 // replaced by D - c * R and its upper neighbour gains c, with
 // c = floor((D + R/2) / R) (the balanced choice; Lemma 1 allows any signed

@@ -15,8 +15,10 @@
 //      either rounds the result (Section 3 steps 6-7) or adds it into a
 //      caller-held accumulator.
 //
-// One persistent CTA per SM; 16-byte read-only streaming loads, double
-// buffered in registers so that each thread keeps two batches in flight.
+// One persistent CTA per SM.  FP64 streams its input through a shared-memory
+// ring of bulk asynchronous copies fed by a producer warp (sum_kernel_tma);
+// FP32 and BF16 use 16-byte read-only loads, double buffered in registers so
+// that each thread keeps two batches in flight (sum_kernel).
 #include <cuda_runtime.h>
 
 #include "digits.cuh"
