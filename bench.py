@@ -621,7 +621,7 @@ def run_ours(args):
         line["config"]["workload"] = f"profiling case: n = 2^{args.log2n}, same recipe"
     line["context"] = {"naive_fp64_sum": naive_sum_context(torch, x, n, result_bits, stream),
                        "paper": PAPER_CONTEXT}
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:  # the oracle is timed at N = 1 only
         line["cpu_baseline"] = cpu_baseline(bits, passes=8, gpu_bits=result_bits)
     if ws == 1 and (args.adaptive or (args.log2n == LOG2N and not args.primary_only)):
         line["adaptive"] = bench_adaptive(es, torch, dev, x, n)
