@@ -10,7 +10,15 @@ C ABI (``exactsum_sum``) with the input already resident in HBM.
 Printed (rank 0, one JSON line): throughput in Gelem/s, the roofline of the
 sum kernel against measured HBM bandwidth, the end-to-end figure through
 ``exactsum_sum_host`` from pinned host memory, the CPU oracle's throughput on
-the host cores, and the SM clocks sampled during the timed region.
+the host cores, and the SM clocks sampled during the timed region.  At N = 1
+the line also carries, each measured after the headline's timed region:
+the condition-number-sensitive path (``adaptive``); the 65,536-segment
+batched sum against one launch per segment, every segment checked against
+the oracle (``segmented``); the served request stream, an oracle sample,
+alone-vs-mix re-submission and the one-launch-per-request baseline
+(``serving``); the FP32 and BF16 single-array sums at full size
+(``narrow``); and the exponent-range sweep over the four dataset families
+(``delta_sweep``).
 
 ``--impl reference`` times the CPU oracle instead (the only baseline this
 method has: the paper publishes no GPU or absolute numbers).
@@ -234,11 +242,12 @@ def naive_sum_context(torch, x, n, exact_bits, stream):
     return out
 
 
-def bench_segmented(es, W, torch, dev, steps, num_segments=65536, per_segment=True):
+def bench_segmented(es, W, torch, dev, steps, num_segments=65536, per_segment=True, check=True):
     """65,536 FP64 segments with log-uniform lengths in [1, 2^20] (Anderson-style
     mean-subtracted Gaussians scaled by 2^k, k uniform in [-200, 200]): the
     batched call (one graph-captured launch sequence, autotuned) against one
-    exactsum_sum launch per segment, same results bit for bit."""
+    exactsum_sum launch per segment, same results bit for bit; afterwards the
+    CPU oracle checks the result of every segment of the timed launch."""
     lengths = W.segment_lengths(num_segments, seed=0)
     off = W.csr_offsets(lengths)
     total = int(off[-1])
@@ -266,11 +275,16 @@ def bench_segmented(es, W, torch, dev, steps, num_segments=65536, per_segment=Tr
         return a.elapsed_time(b) / k
 
     batched_ms = timed(lambda: es.segmented_sum(x, d_off, out=out_b), max(3, steps))
+    torch.cuda.synchronize(dev)
+    batched_bits = out_b.view(torch.int64).cpu().numpy().view(np.uint64)
     if per_segment:
         each_ms = timed(lambda: es.sum_each(x, h_off, out=out_e), 2)
         same = bool(torch.equal(out_b.view(torch.int64), out_e.view(torch.int64)))
     else:
         each_ms, same = float("nan"), None
+    t_chk = time.perf_counter()
+    mism = oracle_check_segments(torch, x, off, batched_bits) if check else None
+    t_chk = time.perf_counter() - t_chk
     r = {"workload": f"{num_segments:,} FP64 segments, lengths log-uniform [1, 2^20] (seed 0), N(0,1)*2^k, "
                      "k in [-200,200], minus the segment mean (device-generated)",
          "segments": len(lengths), "elements": total, "bytes": total * 8,
@@ -280,15 +294,63 @@ def bench_segmented(es, W, torch, dev, steps, num_segments=65536, per_segment=Tr
          "batched_hbm_gbs": round(total * 8 / batched_ms / 1e6, 1),
          "tuned": {"warps": warps, "reducer": ["register", "tma", "window"][kind], "tile": tile, "ms": round(tune_ms, 3)},
          "bit_identical_to_per_segment": same}
+    if check:
+        r["oracle_checked"] = len(lengths)
+        r["oracle_mismatches"] = len(mism)
+        r["oracle_first_mismatches"] = mism[:8]
+        r["oracle_check"] = (f"every segment of the timed (autotuned) launch against the CPU oracle: input copied "
+                             f"to the host in chunks of <= 2^27 elements, {os.cpu_count()} threads, {t_chk:.1f} s")
     del x
     torch.cuda.empty_cache()
     return r
 
 
-def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_steps=2, max_slots=128):
+def oracle_check_segments(torch, x, off, got_bits, chunk_elems=1 << 27):
+    """Compare every segment's result bits with the CPU oracle (test
+    infrastructure, run after the timed region).  The device input is
+    copied to the host in chunks of whole segments; within a chunk the
+    segments are spread over the host cores, one oracle thread each.
+    Returns the indices of the segments that differ."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    threads = os.cpu_count() or 1
+    S = len(off) - 1
+    bad = []
+    with ThreadPoolExecutor(threads) as pool:
+        s = 0
+        while s < S:
+            e = s + 1
+            while e < S and off[e + 1] - off[s] <= chunk_elems:
+                e += 1
+            lo, hi = int(off[s]), int(off[e])
+            host = x[lo:hi].cpu().numpy().view(np.uint64)
+            # groups of consecutive segments with about equal element counts
+            rel = off[s:e + 1] - lo
+            cuts = np.searchsorted(rel, np.linspace(0, hi - lo, threads + 1)[1:-1])
+            bounds = sorted(set([0, *cuts.tolist(), e - s]))
+            futs = [(a, pool.submit(oracle.exact_sum_segmented, host, rel[a:b + 1], 0, 0, 0, 1))
+                    for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+            for a, f in futs:
+                want = f.result().astype(np.uint64)
+                got = got_bits[s + a:s + a + len(want)]
+                bad.extend((np.nonzero(want != got)[0] + s + a).tolist())
+            s = e
+    return bad
+
+
+def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_steps=2, max_slots=128,
+                  check=True, per_request=True):
     """Poisson stream of requests at 20k req/s (mean gap 50 us), sizes
     floor(2^(10 + 16U)), FP64 with p = 0.8 else FP32, windows into 2^26-element
-    uniform [-1,1) device pools; served by the continuous-batching engine."""
+    uniform [-1,1) device pools; served by the continuous-batching engine.
+
+    Afterwards: the CPU oracle checks 1,000 random requests plus the 50
+    largest; 100 sampled requests are submitted again, each alone, and must
+    give the same bits; and the same stream, with the same arrival times, is
+    replayed as one exactsum_sum launch per request (the baseline the engine
+    is measured against), whose results must equal the served ones for
+    every request."""
     if num_requests <= 0:
         return None
     req = W.serving_requests(num_requests, seed=0)
@@ -297,23 +359,28 @@ def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_st
          es.F32: torch.from_numpy(pools[es.F32].view(np.int32)).to(dev)}
     base = {k: v.data_ptr() for k, v in d.items()}
     isz = {es.F64: 8, es.F32: 4}
+    mask = {es.F64: (1 << 64) - 1, es.F32: (1 << 32) - 1}
     budget = 4 << 30
+    ns, dts, offs, arr = (req["n"].tolist(), req["dtype"].tolist(), req["offset"].tolist(),
+                          req["arrival_us"].tolist())
+    N = len(ns)
+    ids = [0] * N
+    alone_mismatch = None
+    alone_idx = np.random.default_rng(1).choice(N, min(100, N), replace=False).tolist()
     server = es.exactsum_server_create(dev.index, max_slots, budget, chunk, 1 << 15, max_steps)
     try:
-        ns, dts, offs, arr = (req["n"].tolist(), req["dtype"].tolist(), req["offset"].tolist(),
-                              req["arrival_us"].tolist())
         # warm the engine with a few requests
-        for k in range(8):
+        for k in range(min(8, N)):
             es.exactsum_server_submit(server, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k], dts[k], es.RNE, 0)
         es.exactsum_server_drain(server, 60_000)
         es.exactsum_server_poll(server)
         t0 = time.perf_counter()
-        for k in range(len(ns)):
+        for k in range(N):
             target = arr[k] * 1e-6
             while time.perf_counter() - t0 < target:
                 pass
-            es.exactsum_server_submit(server, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k], dts[k],
-                                      es.RNE, 0)
+            ids[k] = es.exactsum_server_submit(server, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k],
+                                               dts[k], es.RNE, 0)
         submit_span = time.perf_counter() - t0
         es.exactsum_server_drain(server, 600_000)
         recs = []
@@ -323,6 +390,18 @@ def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_st
                 break
             recs.extend(got)
         stats = es.exactsum_server_stats(server)
+        by_id = {r.id: r for r in recs}
+        served = [by_id[i].result_bits & mask[dts[k]] if i in by_id else None for k, i in enumerate(ids)]
+        if check:
+            # the same request submitted alone gives the same bits
+            alone_mismatch = 0
+            for k in alone_idx:
+                rid = es.exactsum_server_submit(server, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k],
+                                                dts[k], es.RNE, 0)
+                es.exactsum_server_drain(server, 60_000)
+                r = [c for c in es.exactsum_server_poll(server) if c.id == rid]
+                if not r or (r[0].result_bits & mask[dts[k]]) != served[k]:
+                    alone_mismatch += 1
     finally:
         es.exactsum_server_destroy(server)
     lat = np.array([r.done_ns - r.submit_ns for r in recs], dtype=np.float64) / 1e3
@@ -330,15 +409,102 @@ def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_st
     first = min(r.submit_ns for r in recs)
     last = max(r.done_ns for r in recs)
     elems = float(sum(ns))
-    return {"workload": "100,000 requests, Poisson 20k req/s, n = floor(2^(10+16U)), 80% FP64 / 20% FP32, "
-                        "windows of 2^26-element uniform [-1,1) device pools (seed 0)",
-            "requests": len(recs), "ok": ok, "offered_req_s": round(len(ns) / submit_span, 1),
+    out = {"workload": "100,000 requests, Poisson 20k req/s, n = floor(2^(10+16U)), 80% FP64 / 20% FP32, "
+                       "windows of 2^26-element uniform [-1,1) device pools (seed 0)",
+           "requests": len(recs), "ok": ok, "offered_req_s": round(N / submit_span, 1),
+           "p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),
+           "mean_us": round(float(lat.mean()), 1), "max_us": round(float(lat.max()), 1),
+           "gelem_s": round(elems / ((last - first) * 1e-9) / 1e9, 2),
+           "engine": {"max_slots": max_slots, "budget_bytes": budget, "chunk_elems": chunk, "tile_elems": 1 << 15,
+                      "max_steps_per_request": max_steps,
+                      "steps": stats["steps"], "peak_resident": stats["peak_active"]}}
+    if check:
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        rng = np.random.default_rng(2)
+        sample = set(rng.choice(N, min(1000, N), replace=False).tolist())
+        sample |= set(np.argsort(np.asarray(ns), kind="stable")[-50:].tolist())
+        sample = sorted(sample)
+        threads = os.cpu_count() or 1
+        t_chk = time.perf_counter()
+
+        def want(k):
+            return oracle.exact_sum(pools[dts[k]][offs[k]:offs[k] + ns[k]], dts[k], dts[k], es.RNE, 1)
+
+        with ThreadPoolExecutor(threads) as pool:
+            wants = list(pool.map(want, sample))
+        bad = [k for k, w in zip(sample, wants) if served[k] != w]
+        out["oracle_checked"] = len(sample)
+        out["oracle_mismatches"] = len(bad)
+        out["oracle_check"] = (f"{len(sample)} requests (1,000 uniformly sampled plus the 50 largest, "
+                               f"{sum(ns[k] for k in sample) / 1e9:.2f}e9 elements) against the CPU oracle, "
+                               f"{threads} threads, {time.perf_counter() - t_chk:.1f} s")
+        out["alone_resubmitted"] = len(alone_idx)
+        out["alone_mismatches"] = alone_mismatch
+    if per_request:
+        base_line = per_request_baseline(es, torch, dev, ns, dts, offs, arr, base, isz)
+        res_bits = base_line.pop("_bits")
+        diff = sum(1 for k in range(N) if served[k] != (int(res_bits[k]) & mask[dts[k]]))
+        base_line["results_identical_to_served"] = diff == 0
+        base_line["results_differing"] = diff
+        out["per_request_baseline"] = base_line
+        out["speedup_vs_per_request"] = {
+            "p50": round(base_line["p50_us"] / out["p50_us"], 3),
+            "p99": round(base_line["p99_us"] / out["p99_us"], 3),
+            "gelem_s": round(out["gelem_s"] / base_line["gelem_s"], 3)}
+    return out
+
+
+def per_request_baseline(es, torch, dev, ns, dts, offs, arr, base, isz, ring=8192):
+    """The serving workload without the engine: the same requests at the same
+    arrival times, each summed by its own exactsum_sum launch on one stream
+    (one handle), its completion observed through a CUDA event polled from
+    the submitting loop.  Latency is launch -> event complete on the host."""
+    import collections
+    lib = es.library()
+    h = es.handle_for(dev.index)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    N = len(ns)
+    res = torch.zeros(N, dtype=torch.int64, device=dev)
+    rp = res.data_ptr()
+    fn = lib.exactsum_sum
+    for k in range(min(8, N)):  # warm
+        fn(h, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k], dts[k], es.RNE, rp + 8 * k, sp)
+    torch.cuda.synchronize(dev)
+    events = [torch.cuda.Event() for _ in range(ring)]
+    sub = [0] * N
+    done = [0] * N
+    arr_ns = [int(a * 1e3) for a in arr]
+    pending = collections.deque()
+    pc = time.perf_counter_ns
+    launches = 0
+    t0 = pc()
+    k = 0
+    while k < N or pending:
+        while pending and pending[0][1].query():
+            j, _ = pending.popleft()
+            done[j] = pc()
+        if k < N and pc() - t0 >= arr_ns[k] and len(pending) < ring:
+            sub[k] = pc()
+            st = fn(h, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k], dts[k], es.RNE, rp + 8 * k, sp)
+            if st != es.OK:
+                raise RuntimeError(f"exactsum_sum failed with status {st}")
+            ev = events[k % ring]
+            ev.record(stream)
+            pending.append((k, ev))
+            launches += 1
+            k += 1
+    torch.cuda.synchronize(dev)
+    lat = (np.asarray(done, dtype=np.float64) - np.asarray(sub, dtype=np.float64)) / 1e3
+    span = (max(done) - min(sub)) * 1e-9
+    return {"impl": "one exactsum_sum launch per request, one stream and handle, same arrival times; "
+                    "completion seen by polling a CUDA event per request",
+            "launches": launches,
             "p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),
             "mean_us": round(float(lat.mean()), 1), "max_us": round(float(lat.max()), 1),
-            "gelem_s": round(elems / ((last - first) * 1e-9) / 1e9, 2),
-            "engine": {"max_slots": max_slots, "budget_bytes": budget, "chunk_elems": chunk, "tile_elems": 1 << 15,
-                       "max_steps_per_request": max_steps,
-                       "steps": stats["steps"], "peak_resident": stats["peak_active"]}}
+            "gelem_s": round(float(sum(ns)) / span / 1e9, 2),
+            "_bits": res.cpu().numpy().view(np.uint64)}
 
 
 def bench_adaptive(es, torch, dev, x, n, reps=3):
@@ -460,56 +626,143 @@ def run_reference(args):
     return 0
 
 
-def run_narrow(args):
+# The integer-ALU pipe of one sub-partition issues one warp instruction every
+# two cycles (16 lanes per cycle): 152 SMs x 4 sub-partitions x 16 lanes x the
+# SM clock is the ALU roof of the kernels that integer decoding binds.
+ALU_LANES_PER_SM_CYCLE = 64
+
+
+def bench_narrow(es, W, torch, dev, dt, steps, warmup, log2n=None, check=True):
     """FP32 or BF16 single-array exact sum on the wide-exponent recipes
     (FP32: n = 2^29, 99% normals with biased exponent uniform in [1, 254] and
     1% subnormals; BF16: n = 2^30, exponent uniform in [-126, 127]), rounded
-    to the input format: device time and roofline only.  These are parity and
-    profiling cases beside the FP64 benchmark line, not the benchmark."""
+    to the input format: device time per launch (CUDA events on the launching
+    stream, inputs of 2 GiB > L2), HBM roofline, clocks, and the result
+    checked against the CPU oracle on the full input."""
+    name = "f32" if dt == es.F32 else "bf16"
+    log2n = log2n if log2n is not None else (29 if dt == es.F32 else 30)
+    n = 1 << log2n
+    eb = 4 if dt == es.F32 else 2
+    t_gen = time.perf_counter()
+    bits = W.wide_f32(n, seed=0) if dt == es.F32 else W.wide_bf16(n, seed=0)
+    t_gen = time.perf_counter() - t_gen
+    x = torch.from_numpy(bits.view(np.int32 if dt == es.F32 else np.int16)).to(dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = es.handle_for(dev.index)
+    for _ in range(max(warmup, 3)):
+        es.exactsum_sum(h, x.data_ptr(), n, dt, dt, es.RNE, out.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with ClockSampler(dev.index) as clocks:
+        for i in range(steps):
+            starts[i].record(stream)
+            es.exactsum_sum(h, x.data_ptr(), n, dt, dt, es.RNE, out.data_ptr(), stream.cuda_stream)
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
+    peak, peak_kind = measured_peaks()
+    achieved = n * eb / (ms * 1e-3) / 1e9
+    result_bits = int(out.view(torch.int64).item()) & ((1 << (8 * eb)) - 1)
+    clk = clocks.summary()
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    alu_roof = es_sm_count(torch, dev) * ALU_LANES_PER_SM_CYCLE * sm_mhz * 1e6
+    r = {"workload": f"{name.upper()} n = 2^{log2n}, wide-exponent recipe (seed 0), rounded to the input format",
+         "n": n, "launches": steps, "ms": round(ms, 4), "gelem_s": round(n / ms / 1e6, 1),
+         "roofline": {"bound": NARROW_BOUND[name], "hbm_achieved": round(achieved, 1), "hbm_peak": peak,
+                      "unit": "GB/s", "hbm_frac": round(achieved / peak, 4),
+                      "peak_kind": f"{peak_kind} (STREAM-style copy)",
+                      "algorithmic_bytes_per_launch": n * eb,
+                      "alu_roof_tera_lane_ops_per_s": round(alu_roof / 1e12, 2),
+                      "alu_roof": "SMs x 4 sub-partitions x 16 ALU lanes per cycle x median SM clock; "
+                                  "instructions per element from ncu are in profiles/"},
+         "clocks": clk, "result_bits": f"{result_bits:#x}"}
+    if check:
+        import oracle
+        t_chk = time.perf_counter()
+        want = oracle.exact_sum(bits, dt, dt, es.RNE, threads=os.cpu_count() or 1)
+        r["gpu_result_equals_oracle"] = result_bits == want
+        r["oracle_check"] = (f"full input, {os.cpu_count()} threads, {time.perf_counter() - t_chk:.1f} s "
+                             f"(input generated in {t_gen:.1f} s)")
+    del x
+    torch.cuda.empty_cache()
+    return r
+
+
+# What bounds each narrow-format kernel (from ncu: pipe utilisation and DRAM
+# throughput of the current kernels).
+NARROW_BOUND = {"f32": "alu", "bf16": "alu"}
+
+
+def es_sm_count(torch, dev) -> int:
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def bench_delta_block(es, W, torch, dev, log2n=26, deltas=(10, 2000, 2046), steps=20, check=True):
+    """A compact form of the delta sweep (the design of the paper's Fig. 2,
+    Section 6.3) on the benchmark kernel: the four dataset families at three
+    exponent ranges, n = 2^26 FP64 (512 MiB, larger than L2), device time per
+    launch and, for each input, the result against the CPU oracle."""
+    n = 1 << log2n
+    h = es.handle_for(dev.index)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream(dev)
+    peak, _ = measured_peaks()
+    rows = []
+    mism = 0
+    for family in (1, 2, 3, 4):
+        for delta in deltas:
+            bits = W.family_f64(family, n, delta, seed=family)
+            x = torch.from_numpy(bits.view(np.int64)).to(dev)
+            for _ in range(3):
+                es.exactsum_sum(h, x.data_ptr(), n, es.F64, es.F64, es.RNE, out.data_ptr(), s.cuda_stream)
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            for _ in range(steps):
+                es.exactsum_sum(h, x.data_ptr(), n, es.F64, es.F64, es.RNE, out.data_ptr(), s.cuda_stream)
+            b.record(s)
+            torch.cuda.synchronize(dev)
+            ms = a.elapsed_time(b) / steps
+            row = {"family": family, "delta": delta, "ms": round(ms, 4), "gelem_s": round(n / ms / 1e6, 1),
+                   "hbm_frac": round(8 * n / ms / 1e6 / peak, 4)}
+            if check:
+                import oracle
+                got = int(out.view(torch.int64).item()) & ((1 << 64) - 1)
+                row["equals_oracle"] = got == oracle.exact_sum(bits, threads=os.cpu_count() or 1)
+                mism += 0 if row["equals_oracle"] else 1
+            rows.append(row)
+            del x
+    return {"n": n, "launches_per_row": steps,
+            "families": {"1": "all positive", "2": "mixed signs", "3": "mixed signs minus the mean",
+                         "4": "exact sum zero (+/- pairs)"},
+            "kernel": "the benchmark kernel (exactsum_sum, FP64 -> FP64, RNE)",
+            "rows": rows, "oracle_mismatches": mism if check else None}
+
+
+def run_narrow(args):
+    """The FP32 / BF16 line alone (profiling runs)."""
     import torch
 
     import paper_1605_05436_gb300 as es
     from paper_1605_05436_gb300 import workloads as W
 
     dt = {"f32": es.F32, "bf16": es.BF16}[args.dtype]
-    log2n = args.log2n if args.log2n is not None else (29 if dt == es.F32 else 30)
-    n = 1 << log2n
-    eb = 4 if dt == es.F32 else 2
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     es.build()
-    bits = W.wide_f32(n, seed=0) if dt == es.F32 else W.wide_bf16(n, seed=0)
-    x = torch.from_numpy(bits.view(np.int32 if dt == es.F32 else np.int16)).to(dev)
-    out = torch.empty(1, dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    h = es.handle_for(0)
-    for _ in range(max(args.warmup, 3)):
-        es.exactsum_sum(h, x.data_ptr(), n, dt, dt, es.RNE, out.data_ptr(), stream.cuda_stream)
-    torch.cuda.synchronize(dev)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(0) as clocks:
-        for i in range(args.steps):
-            starts[i].record(stream)
-            es.exactsum_sum(h, x.data_ptr(), n, dt, dt, es.RNE, out.data_ptr(), stream.cuda_stream)
-            ends[i].record(stream)
-        torch.cuda.synchronize(dev)
-    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps
-    peak, peak_kind = measured_peaks()
-    achieved = n * eb / (ms * 1e-3) / 1e9
+    r = bench_narrow(es, W, torch, dev, dt, args.steps, args.warmup, args.log2n, check=not args.no_check)
     line = {"metric": f"exact-sum Gelem/s ({args.dtype.upper()}, profiling case)",
-            "value": round(n / ms / 1e6, 3), "unit": "Gelem/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "value": r["gelem_s"], "unit": "Gelem/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
             "dtype": "int64" if dt == es.F32 else "int32", "data": "synthetic",
-            "config": {"workload": f"{args.dtype.upper()} n = 2^{log2n}, wide-exponent recipe (seed 0), "
-                                   "rounded to the input format",
-                       "launch": "exactsum_sum, one kernel per step"},
-            "roofline": {"bound": "alu", "hbm_achieved": round(achieved, 1), "hbm_peak": peak,
-                         "unit": "GB/s", "hbm_frac": round(achieved / peak, 4),
-                         "peak_kind": f"{peak_kind} (STREAM-style copy)",
-                         "algorithmic_bytes_per_launch": n * eb},
-            "gpu_launches": args.steps, "clocks": clocks.summary(),
-            "result_bits": f"{int(out.view(torch.int64).item()) & ((1 << (8 * eb)) - 1):#x}"}
+            "config": {"workload": r["workload"], "launch": "exactsum_sum, one kernel per step"},
+            "roofline": r["roofline"], "gpu_launches": args.steps, "clocks": r["clocks"],
+            "result_bits": r["result_bits"]}
+    if "gpu_result_equals_oracle" in r:
+        line["gpu_result_equals_oracle"] = r["gpu_result_equals_oracle"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -633,8 +886,16 @@ def run_ours(args):
         del x
         torch.cuda.empty_cache()
         line["segmented"] = bench_segmented(es, W, torch, dev, args.steps, args.segments,
-                                            not args.no_per_segment)
-        line["serving"] = bench_serving(es, W, torch, dev, args.requests)
+                                            not args.no_per_segment, check=not args.no_check)
+        line["serving"] = bench_serving(es, W, torch, dev, args.requests, check=not args.no_check,
+                                        per_request=not args.no_per_request)
+        if not args.no_narrow:
+            line["narrow"] = {"f32": bench_narrow(es, W, torch, dev, es.F32, args.steps, args.warmup,
+                                                  check=not args.no_check),
+                              "bf16": bench_narrow(es, W, torch, dev, es.BF16, args.steps, args.warmup,
+                                                   check=not args.no_check)}
+        if not args.no_delta:
+            line["delta_sweep"] = bench_delta_block(es, W, torch, dev, check=not args.no_check)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -660,6 +921,12 @@ def main():
                     help="print the exponent-range sweep over the four dataset families instead")
     ap.add_argument("--requests", type=int, default=100_000,
                     help="requests of the serving measurement (0 skips it)")
+    ap.add_argument("--no-check", action="store_true",
+                    help="skip the CPU-oracle checks after the timed regions (profiling runs)")
+    ap.add_argument("--no-per-request", action="store_true",
+                    help="skip the one-launch-per-request serving baseline")
+    ap.add_argument("--no-narrow", action="store_true", help="skip the FP32/BF16 block of the default line")
+    ap.add_argument("--no-delta", action="store_true", help="skip the delta-sweep block of the default line")
     ap.add_argument("--adaptive", action="store_true",
                     help="also time the condition-number-sensitive path with --primary-only or --log2n")
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64",

@@ -64,19 +64,31 @@ extern "C" {
 #endif
 
 struct CUstream_st;
-/* A CUDA stream handle (the same type as cudaStream_t); NULL is the legacy
- * default stream. */
+/* A CUDA stream.  This is the very type of the CUDA runtime's cudaStream_t
+ * (and of the driver's CUstream), declared here so that the header needs no
+ * CUDA include: a cudaStream_t converts to it without a cast.  NULL is the
+ * legacy default stream. */
 typedef struct CUstream_st* exactsum_stream_t;
 
 typedef struct exactsum_ctx* exactsum_t;
 
-typedef enum { EXACTSUM_F64 = 0, EXACTSUM_F32 = 1, EXACTSUM_BF16 = 2 } exactsum_dtype;
+/* Element formats and rounding modes.  Both enums are passed as 32-bit
+ * integers; the *_MAX_ENUM entries are not values, they only fix the enums'
+ * range to the full 32-bit width so that an out-of-range argument reaches
+ * the library's check (EXACTSUM_EINVAL) instead of being undefined. */
+typedef enum {
+    EXACTSUM_F64 = 0,   /* IEEE 754 binary64 */
+    EXACTSUM_F32 = 1,   /* IEEE 754 binary32 */
+    EXACTSUM_BF16 = 2,  /* bfloat16 (the upper half of a binary32) */
+    EXACTSUM_DTYPE_MAX_ENUM = 0x7FFFFFFF
+} exactsum_dtype;
 
 typedef enum {
     EXACTSUM_RNE = 0,   /* to nearest, ties to even */
     EXACTSUM_RTZ = 1,   /* toward zero */
     EXACTSUM_RUP = 2,   /* toward +infinity */
-    EXACTSUM_RDOWN = 3  /* toward -infinity */
+    EXACTSUM_RDOWN = 3, /* toward -infinity */
+    EXACTSUM_ROUND_MAX_ENUM = 0x7FFFFFFF
 } exactsum_round;
 
 typedef enum {
@@ -105,7 +117,12 @@ typedef enum {
 /* Handle                                                                  */
 /* ---------------------------------------------------------------------- */
 
-/* Create a handle on CUDA device `device` (which becomes current on the
+/* A handle serves every call below that computes the problem of Section 1
+ * (given X = {x_1..x_n}, return a rounding of S_n = sum x_i): it owns the
+ * workspace in which the reducers' partial accumulators meet before the
+ * single post-process rounding (Section 6.1), so that no call allocates.
+ *
+ * Create a handle on CUDA device `device` (which becomes current on the
  * calling thread) and allocate its workspace.  `max_segments_hint` sizes
  * the segmented-sum workspace up front (0: grow on first use; growth
  * happens outside any stream capture).  On success *out receives the
@@ -113,7 +130,8 @@ typedef enum {
  * compute capability 10.3. */
 exactsum_status exactsum_create(exactsum_t* out, int device, int64_t max_segments_hint);
 
-/* Free the handle's workspace (after synchronising its device). NULL is OK. */
+/* Free the handle's workspace (after synchronising its device; Section 1
+ * problem statement, as for exactsum_create).  NULL is OK. */
 exactsum_status exactsum_destroy(exactsum_t h);
 
 /* Message for the last failing call on `h` (or on a NULL handle); never
@@ -128,15 +146,15 @@ const char* exactsum_last_error(exactsum_t h);
 /* d_result (one element of out_dtype, device) <- round(sum of d_x[0..n)).
  * d_x: n elements of in_dtype in device memory (may be NULL when n == 0).
  * One kernel launch; no host synchronisation. */
-exactsum_status exactsum_sum(exactsum_t h, const void* d_x, int64_t n, int in_dtype,
-                             int out_dtype, int mode, void* d_result, exactsum_stream_t stream);
+exactsum_status exactsum_sum(exactsum_t h, const void* d_x, int64_t n, exactsum_dtype in_dtype,
+                             exactsum_dtype out_dtype, exactsum_round mode, void* d_result, exactsum_stream_t stream);
 
 /* End-to-end variant with host buffers: copies h_x to the device in
  * pipelined chunks on `stream`, sums it, copies the rounded result to
  * h_result (one element of out_dtype), and waits for the stream.  The
  * device copy buffers belong to the handle. */
-exactsum_status exactsum_sum_host(exactsum_t h, const void* h_x, int64_t n, int in_dtype,
-                                  int out_dtype, int mode, void* h_result,
+exactsum_status exactsum_sum_host(exactsum_t h, const void* h_x, int64_t n, exactsum_dtype in_dtype,
+                                  exactsum_dtype out_dtype, exactsum_round mode, void* h_result,
                                   exactsum_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
@@ -162,8 +180,8 @@ exactsum_status exactsum_sum_host(exactsum_t h, const void* h_x, int64_t n, int 
  * null) <- r of the pass that stopped, 0 if the exact kernel ran.  Errors
  * as for exactsum_sum; the handle's per-pass state (64 bytes of device and
  * page-locked host memory) is allocated on first use. */
-exactsum_status exactsum_sum_adaptive(exactsum_t h, const void* d_x, int64_t n, int in_dtype,
-                                      int out_dtype, int mode, void* d_result, int* passes,
+exactsum_status exactsum_sum_adaptive(exactsum_t h, const void* d_x, int64_t n, exactsum_dtype in_dtype,
+                                      exactsum_dtype out_dtype, exactsum_round mode, void* d_result, int* passes,
                                       int* last_r, exactsum_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
@@ -180,13 +198,13 @@ exactsum_status exactsum_acc_zero(exactsum_t h, void* d_acc, exactsum_stream_t s
  * accumulator must use the same in_dtype.  The digits are regularised
  * after each call (|digit| <= 2^32), so up to 2^30 accumulators can be
  * merged by plain addition. */
-exactsum_status exactsum_acc_add(exactsum_t h, const void* d_x, int64_t n, int in_dtype,
+exactsum_status exactsum_acc_add(exactsum_t h, const void* d_x, int64_t n, exactsum_dtype in_dtype,
                                  void* d_acc, exactsum_stream_t stream);
 
 /* d_result (one element of out_dtype) <- round(value of d_acc), where d_acc
  * holds sums of in_dtype elements.  d_acc is not modified. */
-exactsum_status exactsum_acc_round(exactsum_t h, const void* d_acc, int in_dtype,
-                                   int out_dtype, int mode, void* d_result,
+exactsum_status exactsum_acc_round(exactsum_t h, const void* d_acc, exactsum_dtype in_dtype,
+                                   exactsum_dtype out_dtype, exactsum_round mode, void* d_result,
                                    exactsum_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
@@ -235,7 +253,7 @@ exactsum_status exactsum_check_timeout(exactsum_t h, uint32_t polls, uint64_t* d
  * (ceil(log2 num_segments)), else a default.  Workspace grows on demand
  * (never during a capture); num_segments < 2^31. */
 exactsum_status exactsum_segmented_sum(exactsum_t h, const void* d_x, const int64_t* d_offsets,
-                                       int64_t num_segments, int in_dtype, int out_dtype, int mode,
+                                       int64_t num_segments, exactsum_dtype in_dtype, exactsum_dtype out_dtype, exactsum_round mode,
                                        void* d_results, exactsum_stream_t stream);
 
 /* The one-launch-per-segment form of the same computation: h_offsets are
@@ -243,7 +261,7 @@ exactsum_status exactsum_segmented_sum(exactsum_t h, const void* d_x, const int6
  * Same results bit for bit; kept as the baseline the batched call is
  * measured against. */
 exactsum_status exactsum_sum_each(exactsum_t h, const void* d_x, const int64_t* h_offsets,
-                                  int64_t num_segments, int in_dtype, int out_dtype, int mode,
+                                  int64_t num_segments, exactsum_dtype in_dtype, exactsum_dtype out_dtype, exactsum_round mode,
                                   void* d_results, exactsum_stream_t stream);
 
 /* Autotuner (synchronous): times each reducer configuration on this very
@@ -256,7 +274,7 @@ exactsum_status exactsum_sum_each(exactsum_t h, const void* d_x, const int64_t* 
  * 2 windowed).
  * d_results_scratch: num_segments elements of in_dtype. */
 exactsum_status exactsum_segmented_autotune(exactsum_t h, const void* d_x, const int64_t* d_offsets,
-                                            int64_t num_segments, int in_dtype,
+                                            int64_t num_segments, exactsum_dtype in_dtype,
                                             void* d_results_scratch, exactsum_stream_t stream,
                                             int* best_warps, int* best_kind, int64_t* best_tile,
                                             float* best_ms);
@@ -320,8 +338,8 @@ exactsum_status exactsum_server_create(exactsum_server_t* out, int device, int m
  * host memory (page-locked for speed); the engine copies it to the device
  * after admission, and x must stay valid until completion.  Thread-safe;
  * returns at once with the request id in *id_out. */
-exactsum_status exactsum_server_submit(exactsum_server_t s, const void* x, int64_t n, int in_dtype,
-                                       int out_dtype, int mode, int x_on_host, uint64_t* id_out);
+exactsum_status exactsum_server_submit(exactsum_server_t s, const void* x, int64_t n, exactsum_dtype in_dtype,
+                                       exactsum_dtype out_dtype, exactsum_round mode, int x_on_host, uint64_t* id_out);
 
 /* Move up to max_out completion records into out; *count receives how many. */
 exactsum_status exactsum_server_poll(exactsum_server_t s, exactsum_completion* out, int max_out,
@@ -354,28 +372,37 @@ exactsum_status exactsum_server_destroy(exactsum_server_t s);
 #define EXACTSUM_NOALLOC_MAX_SEGMENTS 2048
 
 /* The same results as exactsum_segmented_sum, for callers that cannot
- * allocate device memory -- code that must not allocate while a stream is
- * being captured, programs whose device memory belongs to a fixed pool or to
- * another framework's allocator, hosts that forbid allocation after
- * start-up.  It needs no handle and calls no cudaMalloc, cudaFree or other
- * allocating routine: its scratch is one fixed array of about 3.4 MB in
- * the library's own device memory, present on every GPU that loads the
- * library until the process exits.
+ * allocate device memory -- a plug-in whose host application owns all device
+ * memory through its own pool or allocator, a program that must keep a fixed
+ * memory footprint, a real-time host that forbids allocation after start-up.
+ * Such callers cannot create a handle (exactsum_create allocates its
+ * workspace).  This call needs no handle and calls no cudaMalloc, cudaFree
+ * or other allocating routine: its scratch is one fixed array of about
+ * 3.4 MB in the library's own device memory, present on every GPU that loads
+ * the library until the process exits.  (The paper has no counterpart: this
+ * is a deployment variant of exactsum_segmented_sum.)
  *   - Runs on the calling thread's current device; arguments as in
  *     exactsum_segmented_sum (device input, device int64 offsets, device
  *     results).
  *   - num_segments must not exceed EXACTSUM_NOALLOC_MAX_SEGMENTS; a larger
  *     call returns EXACTSUM_EINVAL (message in exactsum_last_error(NULL))
  *     and enqueues nothing.  Inputs up to 512 GiB are covered.
+ *   - Invalid offsets (offsets[s+1] < offsets[s] or offsets[s] < 0) give a
+ *     quiet NaN for that segment; no status word is reported (there is no
+ *     handle to read it through), so check offsets beforehand when a NaN
+ *     result must mean NaN data.
  *   - All calls share the one scratch array and each call clears the parts
  *     that must start at zero: calls whose work overlaps on the GPU race,
  *     so order them (for example on one stream).
  *   - The first call on each device looks up the scratch array's device
- *     address; make that first call before any stream capture starts.
- *   - Asynchronous on `stream`; no graph capture of its own. */
+ *     address and keeps it for the life of the process; make that first
+ *     call before any stream capture starts, and do not use this entry point
+ *     after cudaDeviceReset on that device (the kept address would be
+ *     stale).
+ *   - Asynchronous on `stream`. */
 exactsum_status exactsum_segmented_sum_noalloc(const void* d_x, const int64_t* d_offsets,
-                                               int64_t num_segments, int in_dtype, int out_dtype,
-                                               int mode, void* d_results, exactsum_stream_t stream);
+                                               int64_t num_segments, exactsum_dtype in_dtype, exactsum_dtype out_dtype,
+                                               exactsum_round mode, void* d_results, exactsum_stream_t stream);
 
 #ifdef __cplusplus
 }

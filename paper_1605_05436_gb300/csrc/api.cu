@@ -106,8 +106,8 @@ const char* exactsum_last_error(exactsum_t h) {
   return h ? h->last_error.c_str() : g_null_handle_error.c_str();
 }
 
-exactsum_status exactsum_sum(exactsum_t h, const void* d_x, int64_t n, int in_dtype, int out_dtype,
-                             int mode, void* d_result, exactsum_stream_t stream) {
+exactsum_status exactsum_sum(exactsum_t h, const void* d_x, int64_t n, exactsum_dtype in_dtype, exactsum_dtype out_dtype,
+                             exactsum_round mode, void* d_result, exactsum_stream_t stream) {
   exactsum_status st = es_check_common(h, d_x, n, in_dtype, out_dtype, mode, d_result);
   if (st != EXACTSUM_OK) return st;
   if ((st = set_device(h)) != EXACTSUM_OK) return st;
@@ -134,7 +134,7 @@ exactsum_status exactsum_acc_zero(exactsum_t h, void* d_acc, exactsum_stream_t s
   return EXACTSUM_OK;
 }
 
-exactsum_status exactsum_acc_add(exactsum_t h, const void* d_x, int64_t n, int in_dtype, void* d_acc,
+exactsum_status exactsum_acc_add(exactsum_t h, const void* d_x, int64_t n, exactsum_dtype in_dtype, void* d_acc,
                                  exactsum_stream_t stream) {
   exactsum_status st = es_check_common(h, d_x, n, in_dtype, -1, -1, d_acc);
   if (st != EXACTSUM_OK) return st;
@@ -154,8 +154,8 @@ exactsum_status exactsum_acc_add(exactsum_t h, const void* d_x, int64_t n, int i
   return EXACTSUM_OK;
 }
 
-exactsum_status exactsum_acc_round(exactsum_t h, const void* d_acc, int in_dtype, int out_dtype,
-                                   int mode, void* d_result, exactsum_stream_t stream) {
+exactsum_status exactsum_acc_round(exactsum_t h, const void* d_acc, exactsum_dtype in_dtype, exactsum_dtype out_dtype,
+                                   exactsum_round mode, void* d_result, exactsum_stream_t stream) {
   exactsum_status st = es_check_common(h, d_acc, 1, in_dtype, out_dtype, mode, d_result);
   if (st != EXACTSUM_OK) return st;
   if (((uintptr_t)d_acc) % 8) return fail(h, EXACTSUM_EINVAL, "accumulator must be 8-byte aligned");
@@ -166,8 +166,8 @@ exactsum_status exactsum_acc_round(exactsum_t h, const void* d_acc, int in_dtype
   return EXACTSUM_OK;
 }
 
-exactsum_status exactsum_sum_host(exactsum_t h, const void* h_x, int64_t n, int in_dtype, int out_dtype,
-                                  int mode, void* h_result, exactsum_stream_t stream) {
+exactsum_status exactsum_sum_host(exactsum_t h, const void* h_x, int64_t n, exactsum_dtype in_dtype, exactsum_dtype out_dtype,
+                                  exactsum_round mode, void* h_result, exactsum_stream_t stream) {
   exactsum_status st = es_check_common(h, h_x, n, in_dtype, out_dtype, mode, h_result);
   if (st != EXACTSUM_OK) return st;
   if ((st = set_device(h)) != EXACTSUM_OK) return st;

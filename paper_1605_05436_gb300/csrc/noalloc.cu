@@ -1,9 +1,9 @@
 // noalloc.cu -- the segmented exact sum for callers that cannot allocate.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a stream
-// capture that must not allocate, programs whose device memory is owned by a
-// fixed pool or by another framework's allocator, and embedded or real-time
-// hosts that forbid allocation after start-up.  They cannot create a handle
+// Some callers cannot call cudaMalloc at all: plug-ins whose host
+// application owns all device memory through its own pool or allocator,
+// programs that must keep a fixed memory footprint, and embedded or
+// real-time hosts that forbid allocation after start-up.  They cannot create a handle
 // (exactsum_create allocates its workspace), so this entry point keeps its
 // scratch in one fixed-size array in the library's own device memory
 // (g_noalloc_scratch below, about 3.4 MB on every GPU that loads the
@@ -20,8 +20,11 @@
 //     (different streams without ordering, or different host threads) race
 //     and give wrong results; order them on one stream;
 //   - the first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture begins.
+//     (cudaGetSymbolAddress) with that device current and keeps it for the
+//     life of the process; make that first call before any stream capture
+//     begins, and do not call this after cudaDeviceReset on that device;
+//   - invalid offsets give NaN for their segment; the status word that
+//     records them lives in the shared scratch and is not reported.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -102,8 +105,8 @@ exactsum_status setup(int dev, DeviceScratch* out) {
 }  // namespace
 
 extern "C" exactsum_status exactsum_segmented_sum_noalloc(const void* d_x, const int64_t* d_offsets,
-                                                          int64_t num_segments, int in_dtype,
-                                                          int out_dtype, int mode, void* d_results,
+                                                          int64_t num_segments, exactsum_dtype in_dtype,
+                                                          exactsum_dtype out_dtype, exactsum_round mode, void* d_results,
                                                           exactsum_stream_t stream) {
   if (in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 2)
     return reject(EXACTSUM_EINVAL, "unknown dtype");

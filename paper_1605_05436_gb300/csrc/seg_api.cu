@@ -199,7 +199,7 @@ void es_segment_free_extra(exactsum_t h) {
 extern "C" {
 
 exactsum_status exactsum_segmented_sum(exactsum_t h, const void* d_x, const int64_t* d_offsets,
-                                       int64_t num_segments, int in_dtype, int out_dtype, int mode,
+                                       int64_t num_segments, exactsum_dtype in_dtype, exactsum_dtype out_dtype, exactsum_round mode,
                                        void* d_results, exactsum_stream_t stream) {
   exactsum_status st = check_seg_args(h, d_x, d_offsets, num_segments, in_dtype, out_dtype, mode, d_results);
   if (st != EXACTSUM_OK) return st;
@@ -211,7 +211,7 @@ exactsum_status exactsum_segmented_sum(exactsum_t h, const void* d_x, const int6
 }
 
 exactsum_status exactsum_segmented_autotune(exactsum_t h, const void* d_x, const int64_t* d_offsets,
-                                            int64_t num_segments, int in_dtype, void* d_results_scratch,
+                                            int64_t num_segments, exactsum_dtype in_dtype, void* d_results_scratch,
                                             exactsum_stream_t stream, int* best_warps, int* best_kind,
                                             int64_t* best_tile, float* best_ms) {
   exactsum_status st =
@@ -350,7 +350,7 @@ exactsum_status exactsum_device_status(exactsum_t h, int64_t* status_out) {
 }
 
 exactsum_status exactsum_sum_each(exactsum_t h, const void* d_x, const int64_t* h_offsets, int64_t num_segments,
-                                  int in_dtype, int out_dtype, int mode, void* d_results,
+                                  exactsum_dtype in_dtype, exactsum_dtype out_dtype, exactsum_round mode, void* d_results,
                                   exactsum_stream_t stream) {
   exactsum_status st = check_seg_args(h, d_x, h_offsets, num_segments, in_dtype, out_dtype, mode, d_results);
   if (st != EXACTSUM_OK) return st;

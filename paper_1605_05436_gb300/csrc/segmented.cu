@@ -20,6 +20,8 @@
 //   seg_sum_kernel     the persistent reducer kernel
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -469,8 +471,11 @@ static void launch_main_tma(const SegArgs& a, int grid, cudaStream_t st) {
 }
 
 static cudaError_t configure_kernels(int dev) {
-  static bool done[64] = {};
-  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  // Several host threads may reach this at once (the handle-free entry point
+  // has no handle to lock): the attribute calls are idempotent, and the flag
+  // is atomic, so concurrent first calls at worst configure twice.
+  static std::atomic<bool> done[64] = {};
+  if (dev >= 0 && dev < 64 && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
   cudaError_t e;
   if ((e = set_attr_t<F64, 8>()) != cudaSuccess) return e;
   if ((e = set_attr_t<F64, 12>()) != cudaSuccess) return e;
@@ -484,7 +489,7 @@ static cudaError_t configure_kernels(int dev) {
   if ((e = set_attr_win_t<F64>()) != cudaSuccess) return e;
   if ((e = set_attr_win_t<F32>()) != cudaSuccess) return e;
   if ((e = set_attr_win_t<BF16>()) != cudaSuccess) return e;
-  if (dev >= 0 && dev < 64) done[dev] = true;
+  if (dev >= 0 && dev < 64) done[dev].store(true, std::memory_order_release);
   return cudaSuccess;
 }
 

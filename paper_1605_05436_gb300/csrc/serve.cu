@@ -451,8 +451,8 @@ exactsum_status exactsum_server_create(exactsum_server_t* out, int device, int m
   return EXACTSUM_OK;
 }
 
-exactsum_status exactsum_server_submit(exactsum_server_t s, const void* x, int64_t n, int in_dtype,
-                                       int out_dtype, int mode, int x_on_host, uint64_t* id_out) {
+exactsum_status exactsum_server_submit(exactsum_server_t s, const void* x, int64_t n, exactsum_dtype in_dtype,
+                                       exactsum_dtype out_dtype, exactsum_round mode, int x_on_host, uint64_t* id_out) {
   if (!s) return EXACTSUM_EINVAL;
   if (in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 2 || mode < 0 || mode > 3)
     return server_fail(s, EXACTSUM_EINVAL, "unknown dtype or mode");

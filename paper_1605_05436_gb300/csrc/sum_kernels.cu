@@ -21,6 +21,8 @@
 // that each thread keeps two batches in flight (sum_kernel).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "digits.cuh"
 #include "finalize.cuh"
 #include "internal.h"
@@ -392,14 +394,14 @@ static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t str
   const void* fn;
   if constexpr (Cfg::TMA) fn = (const void*)sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S>;
   else fn = (const void*)sum_kernel<DT, Cfg::T, Cfg::U, D>;
-  static bool configured[64] = {};
+  static std::atomic<bool> configured[64] = {};  // idempotent set-up; atomic for concurrent first calls
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || !configured[dev]) {
+  if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) configured[dev] = true;
+    if (dev >= 0 && dev < 64) configured[dev].store(true, std::memory_order_release);
   }
   // at least two vectors per column per CTA, at most one CTA per SM
   const int64_t want = (a.nvec + 2 * COLS - 1) / (2 * COLS);

@@ -27,6 +27,8 @@
 // exact single-pass kernel, which is the untruncated case.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstring>
 
 #include "../../include/exactsum.h"
@@ -373,14 +375,14 @@ __global__ void __launch_bounds__(TR_T, 1) trunc_sum_kernel(TruncArgs a) {
 template <int DT, int R>
 static cudaError_t launch_trunc_t(const TruncArgs& a, int max_ctas, cudaStream_t stream) {
   constexpr size_t SMEM = (size_t)R * TR_T * sizeof(int64_t);
-  static bool configured[64] = {};
+  static std::atomic<bool> configured[64] = {};  // idempotent set-up; atomic for concurrent first calls
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || !configured[dev]) {
+  if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(trunc_sum_kernel<DT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) configured[dev] = true;
+    if (dev >= 0 && dev < 64) configured[dev].store(true, std::memory_order_release);
   }
   const int64_t want = (a.nvec + 2 * TR_T - 1) / (2 * TR_T);
   const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
@@ -407,8 +409,8 @@ static cudaError_t launch_trunc(int in_dt, int R, const TruncArgs& a, int max_ct
 
 }  // namespace es
 
-extern "C" exactsum_status exactsum_sum_adaptive(exactsum_t h, const void* d_x, int64_t n, int in_dtype,
-                                                 int out_dtype, int mode, void* d_result, int* passes,
+extern "C" exactsum_status exactsum_sum_adaptive(exactsum_t h, const void* d_x, int64_t n, exactsum_dtype in_dtype,
+                                                 exactsum_dtype out_dtype, exactsum_round mode, void* d_result, int* passes,
                                                  int* last_r, exactsum_stream_t stream) {
   exactsum_status st = es_check_common(h, d_x, n, in_dtype, out_dtype, mode, d_result);
   if (st != EXACTSUM_OK) return st;

@@ -75,3 +75,29 @@ def test_clock_summary_flags_throttling():
     assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     s.lines = []
     assert s.summary()["reasons"] == ["unavailable"]
+
+
+def test_segment_check_finds_every_planted_mismatch():
+    """The bench's full oracle check of the segmented results (run here on a
+    CPU tensor): correct bits pass, and each altered result is reported,
+    across chunk and thread-group boundaries."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+
+    import bench
+    import oracle
+    from paper_1605_05436_gb300 import workloads as W
+    lengths = W.segment_lengths(300, seed=3, log2_max=12)
+    lengths[::11] = 0
+    off = W.csr_offsets(lengths)
+    bits = W.segmented_f64(lengths, seed=4)
+    x = torch.from_numpy(bits.view(np.int64))
+    good = oracle.exact_sum_segmented(bits, off, threads=2).astype(np.uint64)
+    assert bench.oracle_check_segments(torch, x, off, good, chunk_elems=5000) == []
+    bad = good.copy()
+    planted = [0, 17, 150, 299]
+    for s in planted:
+        bad[s] ^= np.uint64(1)
+    assert bench.oracle_check_segments(torch, x, off, bad, chunk_elems=5000) == planted
+    assert bench.oracle_check_segments(torch, x, off, bad, chunk_elems=1 << 30) == planted

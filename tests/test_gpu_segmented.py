@@ -3,8 +3,8 @@
 Bit-exact: every segment's result equals the oracle's.  Cases cover empty
 segments, tile boundaries, unaligned segment starts, a non-zero first offset,
 invalid offsets (NaN plus a device status bit), graph replay, the autotuner,
-and the 65,536-segment Anderson-style workload (1/16 scale in full, full
-size on sampled segments)."""
+and the 65,536-segment Anderson-style workload (1/16 scale, and full size
+on the benchmark's reducer, every segment checked)."""
 from __future__ import annotations
 
 import numpy as np
@@ -180,21 +180,28 @@ def test_anderson_sixteenth_scale():
     assert np.array_equal(np.array(G.result_bits(got, es.F64), dtype=np.uint64), want.astype(np.uint64))
 
 
-def test_anderson_full_sampled(anderson_full):
-    """65,536 segments (about 5e9 elements, 40 GB), launched as the benchmark
-    launches it; the oracle checks a sample of segments including the longest
-    and a run of short ones."""
+def test_anderson_full_every_segment(anderson_full, tmp_path):
+    """65,536 segments (about 5e9 elements, 40 GB) on the reducer the
+    benchmark's autotuner picks for this workload (windowed, 16 warps,
+    131,072-element tiles), launched as the benchmark launches it; the oracle
+    checks every segment, and the handle's default reducer must agree."""
+    import bench
     lengths, off, x = anderson_full
     d_off = torch.from_numpy(off).to(DEV)
-    got = es.segmented_sum(x, d_off)
-    torch.cuda.synchronize()
+    h = es.handle_for(0)
+    S = len(lengths)
+    try:
+        _force_reducer(h, tmp_path, es.F64, S, 2, 131072)
+        got = es.segmented_sum(x, d_off)
+        torch.cuda.synchronize()
+    finally:
+        _restore_default(h, tmp_path, es.F64, S)
     got_bits = np.array(G.result_bits(got, es.F64), dtype=np.uint64)
-    rng = np.random.default_rng(0)
-    sample = set(rng.choice(len(lengths), 48, replace=False).tolist())
-    sample |= set(np.argsort(lengths)[-8:].tolist()) | set(range(100, 116))
-    for s in sorted(sample):
-        seg = x[int(off[s]):int(off[s + 1])].cpu().numpy().view(np.uint64)
-        assert int(got_bits[s]) == oracle.exact_sum(seg, threads=16), s
+    assert bench.oracle_check_segments(torch, x, off, got_bits) == []
+    default = es.segmented_sum(x, d_off)
+    torch.cuda.synchronize()
+    assert np.array_equal(np.array(G.result_bits(default, es.F64), dtype=np.uint64), got_bits)
+    assert es.exactsum_device_status(h) == 0
 
 
 REDUCERS = {1: "tma", 2: "window"}

@@ -36,8 +36,10 @@ def _case(seed, num_segments, dt):
     off = W.csr_offsets(lengths)
     if dt == es.F64:
         bits = W.segmented_f64(lengths, seed=seed + 1)
-    else:
+    elif dt == es.F32:
         bits = W.wide_f32(int(off[-1]), seed=seed + 1)
+    else:
+        bits = W.wide_bf16(int(off[-1]), seed=seed + 1)
     return bits, off
 
 
@@ -50,7 +52,9 @@ def _noalloc(x, d_off, num_segments, in_dt, out_dt, mode):
 
 def test_noalloc_matches_regular_entry_point_twice():
     cases = [(_case(3, es.NOALLOC_MAX_SEGMENTS, es.F64), es.F64, es.F64, es.RNE),
-             (_case(9, 1000, es.F32), es.F32, es.F64, es.RDOWN)]
+             (_case(9, 1000, es.F32), es.F32, es.F64, es.RDOWN),
+             (_case(5, 777, es.BF16), es.BF16, es.BF16, es.RNE),
+             (_case(7, 500, es.F64), es.F64, es.F32, es.RTZ)]
     for (bits, off), in_dt, out_dt, mode in cases:
         x = G.to_device(bits, in_dt, DEV)
         d_off = torch.from_numpy(off).to(DEV)
@@ -63,6 +67,21 @@ def test_noalloc_matches_regular_entry_point_twice():
         assert np.array_equal(gb, rb)
         want = oracle.exact_sum_segmented(bits, off, in_dt, out_dt, mode, threads=8).astype(np.uint64)
         assert np.array_equal(gb, want)
+
+
+def test_noalloc_bad_offsets_give_nan():
+    """A segment whose end precedes its start gives a quiet NaN (no status is
+    reported on this path); the valid segments beside it are exact."""
+    bits = W.uniform_f64(1000, 1)
+    x = G.to_device(bits, es.F64, DEV)
+    off = np.array([0, 100, 50, 1000], dtype=np.int64)
+    d_off = torch.from_numpy(off).to(DEV)
+    got = _noalloc(x, d_off, 3, es.F64, es.F64, es.RNE)
+    torch.cuda.synchronize()
+    gb = G.result_bits(got, es.F64)
+    assert (gb[1] & 0x7FF0000000000000) == 0x7FF0000000000000 and gb[1] & 0xFFFFFFFFFFFFF
+    assert gb[0] == oracle.exact_sum(bits[0:100])
+    assert gb[2] == oracle.exact_sum(bits[50:1000])
 
 
 def test_noalloc_rejects_too_many_segments():
