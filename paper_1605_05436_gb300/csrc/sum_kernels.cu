@@ -24,12 +24,24 @@
 #include <atomic>
 
 #include "digits.cuh"
+#include "fdigits.cuh"
 #include "finalize.cuh"
 #include "internal.h"
 #include "stream.cuh"
 #include "tma.cuh"
 
 namespace es {
+
+// BF16 FP32-digit kernel options (measured): batches of L2 prefetch ahead of
+// the register loads, and the number of FP32 digit sets per thread (2: the
+// two elements of a 32-bit word go to different sets, so their additions
+// do not wait on each other).
+#ifndef ES_BF16F_PD
+#define ES_BF16F_PD 0
+#endif
+#ifndef ES_BF16F_SETS
+#define ES_BF16F_SETS 1
+#endif
 
 // Elements owned by thread t of CTA b: vectors vb + t + j*T (< ve), the
 // unaligned head (CTA 0) and the ragged tail (last CTA).
@@ -50,7 +62,10 @@ __device__ uint32_t rescan_flags(const SumArgs& a, int64_t vb, int64_t ve) {
 // CTA merge and grid merge, shared by both single-array kernels.  Called by
 // every thread of the CTA after its flags are in blk_flags and a barrier.
 // TC threads own digit columns (digit-major, stride TC); NW warps take part.
-template <int DT, int TC, int NW, typename D>
+// HALF: the columns count in half units of the input format (the BF16
+// FP32-digit columns, fdigits.cuh); their exact sum is even and is halved
+// here, digit by digit, before it leaves the CTA.
+template <int DT, int TC, int NW, typename D, bool HALF = false>
 __device__ __forceinline__ void finish_cta(const SumArgs& a, D* cols, int64_t* blk, uint32_t* limbs,
                                            uint32_t blk_flags, uint32_t* is_last) {
   static_assert(Geometry<DT>::DIGITS * TC * sizeof(D) >= NW * ACC_WORDS * sizeof(int64_t),
@@ -68,6 +83,18 @@ __device__ __forceinline__ void finish_cta(const SumArgs& a, D* cols, int64_t* b
   if (t < ACC_WORDS - ACC_DIGITS)
     blk[ACC_DIGITS + t] = flag_word(ACC_DIGITS + t, blk_flags, blockIdx.x == 0 ? a.n : 0);
   __syncthreads();
+  if constexpr (HALF) {
+    // V = sum D_i 2^(32 i) is even, so D_0 is even and
+    // V / 2 = sum ((D_i >> 1) + (D_(i+1) & 1) 2^31) 2^(32 i)
+    int64_t v = 0, up = 0;
+    if (t < ACC_DIGITS) {
+      v = blk[t];
+      up = (t + 1 < ACC_DIGITS) ? blk[t + 1] : 0;
+    }
+    __syncthreads();
+    if (t < ACC_DIGITS) blk[t] = (v >> 1) + ((up & 1) << 31);
+    __syncthreads();
+  }
   if (t < ACC_WORDS) a.partials[blockIdx.x * ACC_WORDS + t] = blk[t];
   __threadfence();
   __syncthreads();
@@ -150,6 +177,125 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   if (flags) atomicOr(&blk_flags, flags);
   __syncthreads();
   finish_cta<DT, T, NW, D>(a, digits, blk, limbs, blk_flags, &is_last);
+}
+
+// BF16 with FP32 digit columns (fdigits.cuh): every thread owns 32 FP32
+// digits, added by one FFMA per element, and 33 int32 digits that take the
+// FP32 digits at each flush (at most FDIG_MAX_ADDS additions per FP32 digit
+// in between).  16-byte read-only loads, double buffered as in sum_kernel.
+// Specials are caught by the flushes (a digit became non-finite); a thread
+// whose digits end all zero saw only zeros or a sum that cancelled, and
+// rescans its elements for the signed-zero flags.
+template <int T, int U>
+__global__ void __launch_bounds__(T, 1) sum_kernel_bf16f(SumArgs a) {
+  constexpr int NW = T / 32;
+  constexpr int EPB = U * 8;  // elements per batch
+  // flush before a batch could take a digit past FDIG_MAX_ADDS additions,
+  // counting the U - 1 leftover vectors and the head and tail element
+  constexpr int FLUSH_BATCHES = (FDIG_MAX_ADDS - 2 - (U - 1) * 8) / EPB;
+  static_assert(FLUSH_BATCHES >= 1, "batch too large for the FP32 digits");
+
+  constexpr int SETS = ES_BF16F_SETS;
+  extern __shared__ int64_t smem_digits[];
+  float* fd = reinterpret_cast<float*>(smem_digits);                     // SETS x 32 x T
+  int32_t* id = reinterpret_cast<int32_t*>(fd + SETS * FDIG_DIGITS * T); // 33 x T
+  __shared__ int64_t blk[ACC_WORDS];
+  __shared__ uint32_t limbs[ACC_DIGITS];
+  __shared__ uint32_t blk_flags, is_last;
+
+  const int t = threadIdx.x;
+  float* fc = fd + t;
+  float* fc1 = fd + (SETS - 1) * FDIG_DIGITS * T + t;
+  int32_t* ic = id + t;
+#pragma unroll 4
+  for (int i = 0; i < SETS * FDIG_DIGITS; ++i) fc[i * T] = 0.0f;
+#pragma unroll 4
+  for (int i = 0; i < FDIG_INT_DIGITS; ++i) ic[i * T] = 0;
+  if (t == 0) blk_flags = 0;
+
+  const uint4* vx = reinterpret_cast<const uint4*>((const char*)a.x + a.head * 2);
+  const int64_t G = gridDim.x;
+  const int64_t vb = a.nvec * blockIdx.x / G, ve = a.nvec * (blockIdx.x + 1) / G;
+  const int64_t cnt = (vb + t < ve) ? (ve - vb - t + T - 1) / T : 0;
+  const uint4* p = vx + vb + t;
+  constexpr int64_t PER = (int64_t)T * U;
+  const int64_t nb = cnt / U;
+  uint32_t spec = 0;
+  int since_flush = 0, flushes = 0;
+  auto flush = [&]() {
+    fdig_flush<T>(fc, ic, spec);
+    if constexpr (SETS == 2) fdig_flush<T>(fc1, ic, spec);
+  };
+  auto add_vec = [&](const uint4& v) {
+    if constexpr (SETS == 2) fdig_add_vec2<T>(fc, fc1, v);
+    else fdig_add_vec<T>(fc, v);
+  };
+  auto after_batch = [&]() {
+    if (++since_flush == FLUSH_BATCHES) {
+      flush();
+      since_flush = 0;
+      if (++flushes == FDIG_REG_FLUSHES / SETS) {
+        fdig_regularise<T>(ic);
+        flushes = 0;
+      }
+    }
+  };
+
+  // ---- hot loop: this thread's vectors vb + t + j*T, double buffered ----
+  // (ES_BF16F_PD > 0: thread 0 also asks for the CTA's batch PD ahead to be
+  // brought into L2, so that the register loads find it there)
+  constexpr int PD = ES_BF16F_PD;
+  const uint4* cta_end = vx + ve;
+  auto prefetch = [&](int64_t kb) {
+    const uint4* q = vx + vb + kb * PER;
+    if (q < cta_end) prefetch_l2(q, (uint32_t)(min(PER, (int64_t)(cta_end - q)) * 16));
+  };
+  if (PD > 0 && t == 0)
+    for (int k = 0; k < PD; ++k) prefetch(k);
+  uint4 A[U], B[U];
+  if (nb > 0) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) A[u] = ldg_stream(p + u * T);
+  }
+  for (int64_t k = 0; k < nb; k += 2) {
+    if (PD > 0 && t == 0) {
+      prefetch(k + PD);
+      prefetch(k + PD + 1);
+    }
+    if (k + 1 < nb) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) B[u] = ldg_stream(p + (k + 1) * PER + u * T);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) add_vec(A[u]);
+    after_batch();
+    if (k + 1 >= nb) break;
+    if (k + 2 < nb) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) A[u] = ldg_stream(p + (k + 2) * PER + u * T);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) add_vec(B[u]);
+    after_batch();
+  }
+  for (int64_t j = nb * U; j < cnt; ++j) add_vec(ldg_stream(p + j * T));
+
+  // ---- unaligned head (CTA 0) and ragged tail (last CTA) ----
+  if (blockIdx.x == 0 && t < a.head) fdig_add_one<T>(fc, (uint32_t)load_one<BF16>(a.x, t));
+  if (blockIdx.x == G - 1 && t < a.tail) fdig_add_one<T>(fc, (uint32_t)load_one<BF16>(a.x, a.n - a.tail + t));
+  flush();
+  fdig_regularise<T>(ic);
+
+  // ---- special values and signed zeros: exact rescan only when needed ----
+  uint32_t any = 0;
+#pragma unroll 4
+  for (int i = 0; i < FDIG_INT_DIGITS; ++i) any |= (uint32_t)ic[i * T];
+  uint32_t flags = 24u;  // a thread with a non-zero digit saw a non-zero element
+  if (spec == 0x7F800000u || any == 0u) flags = rescan_flags<BF16, T>(a, vb, ve);
+  __syncthreads();
+  if (flags) atomicOr(&blk_flags, flags);
+  __syncthreads();
+  finish_cta<BF16, T, NW, int32_t, true>(a, id, blk, limbs, blk_flags, &is_last);
 }
 
 // TMA-streaming form: one producer warp moves the CTA's range through a ring
@@ -352,6 +498,17 @@ struct SumConfig;
 #ifndef ES_BF16_SPLIT
 #define ES_BF16_SPLIT 1
 #endif
+// BF16 with FP32 digit columns added on the FMA pipe (fdigits.cuh):
+// sum_kernel_bf16f<ES_BF16F_T, ES_BF16F_U>; 0 selects the integer columns above.
+#ifndef ES_BF16_FFMA
+#define ES_BF16_FFMA 1
+#endif
+#ifndef ES_BF16F_T
+#define ES_BF16F_T 768
+#endif
+#ifndef ES_BF16F_U
+#define ES_BF16F_U 4
+#endif
 template <> struct SumConfig<F64> {
   static constexpr int TMA = ES_F64_TMA, C = ES_F64_C, TU = ES_F64_TU, S = ES_F64_S, T = ES_F64_T, U = ES_F64_U;
   using Digit = int64_t;
@@ -379,8 +536,35 @@ template <> struct SumConfig<BF16> {
 #endif
 };
 
+// Set the dynamic shared-memory limit of a kernel once per device.
+static cudaError_t configure_once(const void* fn, size_t smem, std::atomic<bool>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64) done[dev].store(true, std::memory_order_release);
+  return cudaSuccess;
+}
+
+static cudaError_t launch_sum_bf16f(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out) {
+  constexpr int T = ES_BF16F_T, U = ES_BF16F_U;
+  constexpr size_t SMEM = (size_t)(ES_BF16F_SETS * FDIG_DIGITS + FDIG_INT_DIGITS) * T * 4;
+  static_assert(SMEM + 2048 <= 232448, "shared memory per CTA");
+  static std::atomic<bool> configured[64] = {};  // idempotent set-up; atomic for concurrent first calls
+  cudaError_t e = configure_once((const void*)sum_kernel_bf16f<T, U>, SMEM, configured);
+  if (e != cudaSuccess) return e;
+  const int64_t want = (a.nvec + 2 * T - 1) / (2 * T);
+  const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
+  if (grid_out) *grid_out = grid;
+  sum_kernel_bf16f<T, U><<<grid, T, SMEM, stream>>>(a);
+  return cudaGetLastError();
+}
+
 template <int DT>
 static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out) {
+  if constexpr (DT == BF16 && ES_BF16_FFMA) return launch_sum_bf16f(a, max_ctas, stream, grid_out);
   using Cfg = SumConfig<DT>;
   using D = typename Cfg::Digit;
   constexpr int ND = ColumnDigits<DT, D>::value;
@@ -395,14 +579,8 @@ static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t str
   if constexpr (Cfg::TMA) fn = (const void*)sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S>;
   else fn = (const void*)sum_kernel<DT, Cfg::T, Cfg::U, D>;
   static std::atomic<bool> configured[64] = {};  // idempotent set-up; atomic for concurrent first calls
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = configure_once(fn, SMEM, configured);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) configured[dev].store(true, std::memory_order_release);
-  }
   // at least two vectors per column per CTA, at most one CTA per SM
   const int64_t want = (a.nvec + 2 * COLS - 1) / (2 * COLS);
   const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));

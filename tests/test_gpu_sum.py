@@ -124,20 +124,28 @@ def _constant_device(bits_value: int, n: int, dt: int):
     return torch.full((n,), int(signed), dtype=G.torch_bits_dtype(dt), device=DEV)
 
 
-@pytest.mark.parametrize("dt,n", [(es.F64, (1 << 27) + 3), (es.F32, (1 << 28) + 5), (es.BF16, (1 << 34) + 7)])
-def test_regularisation_bound(dt, n):
+@pytest.mark.parametrize("dt,n,E", [(es.F64, (1 << 27) + 3, 1024), (es.F32, (1 << 28) + 5, 8),
+                                    (es.BF16, (1 << 34) + 7, 8), (es.BF16, (1 << 34) + 7, 15),
+                                    (es.BF16, (1 << 30) + 7, 254)])
+def test_regularisation_bound(dt, n, E):
     """Adversarial inputs at the deferred-carry headroom: every element adds
     the largest possible value to one digit (mantissa all ones at the
     largest in-digit offset), all positive, all negative, and then with
     alternating signs.  n is large enough that each thread regularises
     mid-stream.  The exact sums are closed forms (n * x, -n * x and x),
-    rounded by the oracle."""
+    rounded by the oracle.  For FP64 and FP32 the largest offset is
+    p = E - 1 with p mod 32 = 31 or p mod 8 = 7; for BF16 both the integer
+    digits' worst case (p mod 8 = 7, E = 8) and the FP32 digits' worst case
+    (E mod 8 = 7, E = 15: each addition adds 255 units of 2^-7 to one FP32
+    digit, the most an addition can) are run, and the largest finite BF16
+    (E = 254, the top FP32 digit, whose carries reach the top int32 digit)."""
     if dt == es.F64:
-        v, unit, m, p = (1024 << 52) | ((1 << 52) - 1), -1074, (1 << 53) - 1, 1023   # p = 32*31 + 31
+        v, unit, m = (E << 52) | ((1 << 52) - 1), -1074, (1 << 53) - 1   # p = 32*31 + 31
     elif dt == es.F32:
-        v, unit, m, p = (8 << 23) | 0x7FFFFF, -149, (1 << 24) - 1, 7                # p & 7 == 7
+        v, unit, m = (E << 23) | 0x7FFFFF, -149, (1 << 24) - 1            # p & 7 == 7
     else:
-        v, unit, m, p = (8 << 7) | 0x7F, -133, (1 << 8) - 1, 7
+        v, unit, m = (E << 7) | 0x7F, -133, (1 << 8) - 1
+    p = E - 1
     sign = 1 << (8 * es.ITEMSIZE[dt] - 1)
     x = _constant_device(v, n, dt)
     for o in (dt, es.F64):
