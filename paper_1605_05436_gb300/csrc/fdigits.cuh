@@ -35,6 +35,10 @@
 
 namespace es {
 
+#ifndef ES_BF16F_PAIR
+#define ES_BF16F_PAIR 0
+#endif
+
 constexpr int FDIG_DIGITS = 32;          // FP32 digits per thread
 constexpr int FDIG_INT_DIGITS = 33;      // int32 radix-2^8 digits per thread (digit 32: carries)
 constexpr int FDIG_MAX_ADDS = 514;       // exact additions per FP32 digit between flushes
@@ -46,19 +50,40 @@ constexpr int FDIG_REG_FLUSHES = 64;     // flushes between int32 regularisation
 // Digit i sits i * STRIDE floats = i * 4 * STRIDE bytes after digit 0; with
 // STRIDE a multiple of 256 that is (i << 10) * (STRIDE / 256) bytes, so the
 // masked exponent bits give the address with one multiply-add.
+// (Other strides: the digit index is shifted down first.)
 template <int STRIDE>
 __device__ __forceinline__ void fdig_add_pair(float* __restrict__ fc, uint32_t w) {
-  static_assert(STRIDE % 256 == 0, "digit stride must be a multiple of 256 floats");
   const uint32_t a0 = w & 0x00007C00u;           // (E0 >> 3) << 10
   const uint32_t a1 = w & 0x7C000000u;           // (E1 >> 3) << 26
   const float x0 = __uint_as_float(w << 16);
   const float x1 = __uint_as_float(w & 0xFFFF0000u);
   const float s0 = __uint_as_float(0x7F000000u - (a0 << 16));
   const float s1 = __uint_as_float(0x7F000000u - a1);
-  float* d0 = (float*)((char*)fc + a0 * (uint32_t)(STRIDE / 256));
-  float* d1 = (float*)((char*)fc + (a1 >> 16) * (uint32_t)(STRIDE / 256));
+  float* d0;
+  float* d1;
+  if constexpr (STRIDE % 256 == 0) {
+    d0 = (float*)((char*)fc + a0 * (uint32_t)(STRIDE / 256));
+    d1 = (float*)((char*)fc + (a1 >> 16) * (uint32_t)(STRIDE / 256));
+  } else {
+    // (a multiply-high of the shifted exponent bits, one FMA-pipe
+    // instruction instead of a shift and a multiply-add, measured 10% slower)
+    d0 = fc + (a0 >> 10) * STRIDE;
+    d1 = fc + (a1 >> 26) * STRIDE;
+  }
+#if ES_BF16F_PAIR
+  // both digits read before either is written, so the two additions do not
+  // wait on each other; when both elements fall in one digit, the upper
+  // element adds onto the lower one's result (and its store comes last)
+  const float v0 = *d0;
+  const float v1 = *d1;
+  const float r0 = __fmaf_rn(x0, s0, v0);
+  const float r1 = __fmaf_rn(x1, s1, d0 == d1 ? r0 : v1);
+  *d0 = r0;
+  *d1 = r1;
+#else
   *d0 = __fmaf_rn(x0, s0, *d0);
   *d1 = __fmaf_rn(x1, s1, *d1);
+#endif
 }
 
 #ifndef ES_BF16F_ADDR
@@ -172,6 +197,52 @@ __device__ __forceinline__ void fdig_flush(float* __restrict__ fc, int32_t* __re
     const int32_t D = __float2int_rn(v * 128.0f);
     ic[i * STRIDE] = (int32_t)((uint32_t)ic[i * STRIDE] + (uint32_t)D);
   }
+}
+
+// The same flush into int32 digits held in registers (I[0..32], the loops
+// fully unrolled so that every index is static).
+template <int STRIDE>
+__device__ __forceinline__ void fdig_flush_regs(float* __restrict__ fc, int32_t (&I)[FDIG_INT_DIGITS],
+                                                uint32_t& spec) {
+#pragma unroll
+  for (int i = 0; i < FDIG_DIGITS; ++i) {
+    const float v = fc[i * STRIDE];
+    fc[i * STRIDE] = 0.0f;
+    spec = max(spec, __float_as_uint(v) & 0x7F800000u);
+    I[i] = (int32_t)((uint32_t)I[i] + (uint32_t)__float2int_rn(v * 128.0f));
+  }
+}
+
+// Warp-transposed flush: lane j takes FP32 digit j of every lane of its warp
+// (columns read rotated by lane, so no two lanes hit one bank), adds them
+// into its own int64 `wd` -- digit j of the warp's radix-2^8 accumulator in
+// half units -- and clears them.  32 lanes x |D| < 2^24 per flush: an int64
+// digit never needs a carry.  `wcols` is this warp's first column.
+template <int STRIDE>
+__device__ __forceinline__ void fdig_flush_warp(float* __restrict__ wcols, int lane, int64_t& wd, uint32_t& spec) {
+  __syncwarp();
+  float* row = wcols + lane * STRIDE;
+#pragma unroll 8
+  for (int l = 0; l < 32; ++l) {
+    const int c = (l + lane) & 31;
+    const float v = row[c];
+    row[c] = 0.0f;
+    spec = max(spec, __float_as_uint(v) & 0x7F800000u);
+    wd += (int64_t)__float2int_rn(v * 128.0f);
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void fdig_regularise_regs(int32_t (&I)[FDIG_INT_DIGITS]) {
+  int32_t carry = 0;
+#pragma unroll
+  for (int i = 0; i < FDIG_INT_DIGITS - 1; ++i) {
+    const int32_t v = I[i] + carry;
+    const int32_t c = (v + 128) >> 8;
+    I[i] = v - (c << 8);
+    carry = c;
+  }
+  I[FDIG_INT_DIGITS - 1] += carry;
 }
 
 }  // namespace es
