@@ -30,6 +30,7 @@ time is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -340,7 +341,7 @@ def oracle_check_segments(torch, x, off, got_bits, chunk_elems=1 << 27):
 
 
 def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_steps=2, max_slots=128,
-                  check=True, per_request=True):
+                  check=True, per_request=True, lanes=None):
     """Poisson stream of requests at 20k req/s (mean gap 50 us), sizes
     floor(2^(10 + 16U)), FP64 with p = 0.8 else FP32, windows into 2^26-element
     uniform [-1,1) device pools; served by the continuous-batching engine.
@@ -369,11 +370,14 @@ def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_st
     alone_idx = np.random.default_rng(1).choice(N, min(100, N), replace=False).tolist()
     server = es.exactsum_server_create(dev.index, max_slots, budget, chunk, 1 << 15, max_steps)
     try:
+        if lanes is not None:
+            es.exactsum_server_set_lanes(server, *lanes)
         # warm the engine with a few requests
         for k in range(min(8, N)):
             es.exactsum_server_submit(server, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k], dts[k], es.RNE, 0)
         es.exactsum_server_drain(server, 60_000)
         es.exactsum_server_poll(server)
+        gc.disable()  # no collector pause inside the timed submission loop
         t0 = time.perf_counter()
         for k in range(N):
             target = arr[k] * 1e-6
@@ -382,6 +386,7 @@ def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_st
             ids[k] = es.exactsum_server_submit(server, base[dts[k]] + offs[k] * isz[dts[k]], ns[k], dts[k],
                                                dts[k], es.RNE, 0)
         submit_span = time.perf_counter() - t0
+        gc.enable()
         es.exactsum_server_drain(server, 600_000)
         recs = []
         while True:
@@ -417,7 +422,12 @@ def bench_serving(es, W, torch, dev, num_requests=100_000, chunk=1 << 21, max_st
            "gelem_s": round(elems / ((last - first) * 1e-9) / 1e9, 2),
            "engine": {"max_slots": max_slots, "budget_bytes": budget, "chunk_elems": chunk, "tile_elems": 1 << 15,
                       "max_steps_per_request": max_steps,
-                      "steps": stats["steps"], "peak_resident": stats["peak_active"]}}
+                      "lanes": {"express_max_bytes": lanes[0], "express_sms": lanes[1],
+                                "resident": lanes[2] if len(lanes) > 2 else 1} if lanes else
+                               "library defaults (express lane: requests up to 4 MiB of input, a resident "
+                               "kernel on 8 SMs; bulk lane: one single-array launch per request on the "
+                               "other SMs)",
+                      "express_kernel_launches": stats["steps"], "peak_resident": stats["peak_active"]}}
     if check:
         import oracle
         from concurrent.futures import ThreadPoolExecutor
@@ -479,6 +489,7 @@ def per_request_baseline(es, torch, dev, ns, dts, offs, arr, base, isz, ring=819
     pending = collections.deque()
     pc = time.perf_counter_ns
     launches = 0
+    gc.disable()  # no collector pause inside the timed loop (it would delay completions)
     t0 = pc()
     k = 0
     while k < N or pending:
@@ -495,6 +506,7 @@ def per_request_baseline(es, torch, dev, ns, dts, offs, arr, base, isz, ring=819
             pending.append((k, ev))
             launches += 1
             k += 1
+    gc.enable()
     torch.cuda.synchronize(dev)
     lat = (np.asarray(done, dtype=np.float64) - np.asarray(sub, dtype=np.float64)) / 1e3
     span = (max(done) - min(sub)) * 1e-9

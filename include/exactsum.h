@@ -349,6 +349,29 @@ exactsum_status exactsum_server_poll(exactsum_server_t s, exactsum_completion* o
  * timeout_ms milliseconds). */
 exactsum_status exactsum_server_drain(exactsum_server_t s, int64_t timeout_ms);
 
+/* Lanes (call before the first exactsum_server_submit; EXACTSUM_EINVAL
+ * afterwards).  A request whose input exceeds express_max_bytes takes the
+ * bulk lane: one launch of the single-array sum kernel (exactsum_sum's) on
+ * all SMs but express_sms, its result rounded straight into pinned host
+ * memory.  Smaller requests take the express lane, on the SMs the bulk lane
+ * leaves free, so that they never wait behind a large request:
+ *   resident = 1 (default): a resident kernel on express_sms SMs takes each
+ *     request from a ring in pinned host memory as soon as it is admitted
+ *     (no launch per request); its tiles are summed by whichever warps are
+ *     free, with the tiles of all requests in flight interleaved (continuous
+ *     batching at tile granularity), and the warp that finishes a request's
+ *     last tile rounds it and publishes the result.  The kernel leaves
+ *     after 5 ms without work and is launched again by the next request;
+ *     while it runs, those SMs are busy polling, so other kernels of the
+ *     process get the remaining SMs;
+ *   resident = 0: continuous-batching steps (one kernel launch per step,
+ *     carrying a chunk of every express request in flight) on the free SMs
+ *     (all SMs while no bulk launch is in flight).
+ * Defaults: 4 MiB, 8 SMs, resident.  express_max_bytes < 0 sends every
+ * request to the express lane; express_sms must be in [1, SMs). */
+exactsum_status exactsum_server_set_lanes(exactsum_server_t s, int64_t express_max_bytes, int express_sms,
+                                         int resident);
+
 /* Counters: steps launched, most requests resident at once, requests not yet complete. */
 exactsum_status exactsum_server_stats(exactsum_server_t s, int64_t* steps, int64_t* peak_active,
                                       int64_t* outstanding);

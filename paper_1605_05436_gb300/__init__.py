@@ -58,6 +58,7 @@ _SIGNATURES = {
     "exactsum_server_submit": [_vp, _vp, _i64, _int, _int, _int, _int, ctypes.POINTER(ctypes.c_uint64)],
     "exactsum_server_poll": [_vp, _vp, _int, ctypes.POINTER(_int)],
     "exactsum_server_drain": [_vp, _i64],
+    "exactsum_server_set_lanes": [_vp, _i64, _int, _int],
     "exactsum_server_stats": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "exactsum_server_destroy": [_vp],
     "exactsum_segmented_sum_noalloc": [_vp, _vp, _i64, _int, _int, _int, _vp, _vp],
@@ -255,6 +256,13 @@ def exactsum_server_poll(server, max_out: int = 4096) -> list:
     cnt = _int(0)
     _check_server(library().exactsum_server_poll(server, buf, max_out, ctypes.byref(cnt)), server)
     return [buf[i] for i in range(cnt.value)]
+
+
+def exactsum_server_set_lanes(server, express_max_bytes: int, express_sms: int, resident: int = 1) -> None:
+    """Bulk/express lane split (before the first submission); express_max_bytes
+    < 0 sends every request to the express lane; resident 1: the express lane
+    is a resident kernel fed from a host ring, 0: continuous-batching steps."""
+    _check_server(library().exactsum_server_set_lanes(server, express_max_bytes, express_sms, resident), server)
 
 
 def exactsum_server_drain(server, timeout_ms: int) -> None:

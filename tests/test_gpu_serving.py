@@ -1,8 +1,9 @@
 """GPU tests of the serving engine (continuous batching of exact-sum
 requests): every result equals the oracle's, a request gives the same bits
 alone and inside a mix, admission honours the memory budget, host-memory
-requests are staged, and requests spanning many steps keep their partial
-sums in their device slots."""
+requests are staged, requests spanning many tiles or steps keep their
+partial sums in their device slots, and every lane configuration (resident
+express kernel, express steps, bulk launches) gives the oracle's bits."""
 from __future__ import annotations
 
 import time
@@ -46,10 +47,17 @@ def pools():
             es.BF16: (p16, G.to_device(p16, es.BF16, DEV))}
 
 
-@pytest.mark.parametrize("max_steps", [0, 3])
-def test_mixed_requests_match_oracle(pools, max_steps):
+@pytest.mark.parametrize("max_steps,lanes", [(0, None), (0, (-1, 16, 0)), (3, (-1, 16, 0)), (3, (1 << 20, 16, 0))],
+                         ids=["default-lanes", "steps-only", "steps-only-max3", "steps-and-bulk"])
+def test_mixed_requests_match_oracle(pools, max_steps, lanes):
+    """Mixed sizes, formats, outputs and modes: with the default lanes (a
+    resident express kernel and the bulk lane), and with the express lane
+    as continuous-batching steps (every request, or beside the bulk lane),
+    where requests span several steps (chunk 2^16, or at most 3 steps)."""
     server = es.exactsum_server_create(0, 64, 1 << 30, 1 << 16, 1 << 12, max_steps)
     try:
+        if lanes:
+            es.exactsum_server_set_lanes(server, *lanes)
         rng = np.random.default_rng(1)
         sizes = [0, 1, 2, 3, 63, 64, 65, 4095, 4096, 4097, 65535, 65536, 65537, 300_001, 1 << 21]
         reqs = {}
@@ -203,3 +211,60 @@ def test_invalid_requests():
         es.exactsum_server_create(0, 0, 1 << 20, 1 << 12, 1 << 12)
     with pytest.raises(es.ExactSumError):
         es.exactsum_server_create(0, 4, 1 << 20, 1000, 64)  # chunk not a multiple of the tile
+
+
+@pytest.mark.parametrize("resident", [1, 0])
+@pytest.mark.parametrize("express_max_bytes", [-1, 0, 1 << 18])
+def test_lanes_match_oracle(pools, express_max_bytes, resident):
+    """Every request through the express lane only (-1), the bulk lane only
+    (0: every non-empty request is larger), and a split at 256 KiB, with
+    the express lane as a resident kernel or as steps, with device- and
+    host-memory inputs, every format, output and mode: each result equals
+    the oracle's, and a request gives the same bits whichever lane it takes."""
+    server = es.exactsum_server_create(0, 64, 1 << 30, 1 << 16, 1 << 12, 2)
+    try:
+        es.exactsum_server_set_lanes(server, express_max_bytes, 16, resident)
+        rng = np.random.default_rng(5)
+        sizes = [0, 1, 7, 4096, 32_769, 65_537, 300_001, 1 << 20, (1 << 21) + 3]
+        reqs, keep = {}, []
+        for k, n in enumerate(sizes * 3):
+            dt = [es.F64, es.F32, es.BF16][k % 3]
+            out = [dt, es.F64, es.F32][(k // 3) % 3]
+            mode = (k * 7) % 4
+            bits, dx = pools[dt]
+            off = int(rng.integers(0, len(bits) - n + 1))
+            if k % 5 == 4 and n:
+                h = torch.from_numpy(bits[off:off + n].view(G.NP_SIGNED[dt]).copy()).pin_memory()
+                keep.append(h)
+                rid = es.exactsum_server_submit(server, h.data_ptr(), n, dt, out, mode, 1)
+            else:
+                rid = es.exactsum_server_submit(server, dx[off:].data_ptr() if n else 0, n, dt, out, mode, 0)
+            reqs[rid] = (bits[off:off + n], dt, out, mode)
+        recs = collect(server, len(reqs))
+        assert len(recs) == len(reqs)
+        for rid, (b, dt, out, mode) in reqs.items():
+            r = recs[rid]
+            assert r.status == es.OK
+            assert r.result_bits < (1 << (8 * es.ITEMSIZE[out]))
+            assert r.result_bits == oracle.exact_sum(b, dt, out, mode, threads=8), (len(b), dt, out, mode)
+    finally:
+        es.exactsum_server_destroy(server)
+
+
+def test_lanes_are_set_before_the_first_request(pools):
+    server = es.exactsum_server_create(0, 8, 1 << 30, 1 << 15, 1 << 12)
+    try:
+        with pytest.raises(es.ExactSumError):
+            es.exactsum_server_set_lanes(server, 1 << 20, 0)
+        with pytest.raises(es.ExactSumError):
+            es.exactsum_server_set_lanes(server, 1 << 20, 100_000)
+        with pytest.raises(es.ExactSumError):
+            es.exactsum_server_set_lanes(server, 1 << 20, 8, 2)
+        es.exactsum_server_set_lanes(server, 1 << 20, 8)
+        bits, dx = pools[es.F64]
+        rid = es.exactsum_server_submit(server, dx.data_ptr(), 1000, es.F64, es.F64, es.RNE, 0)
+        with pytest.raises(es.ExactSumError):
+            es.exactsum_server_set_lanes(server, 1 << 22, 16)
+        assert collect(server, 1)[rid].result_bits == oracle.exact_sum(bits[:1000], threads=2)
+    finally:
+        es.exactsum_server_destroy(server)
