@@ -363,7 +363,13 @@ exactsum_status exactsum_server_drain(exactsum_server_t s, int64_t timeout_ms);
  *     last tile rounds it and publishes the result.  The kernel leaves
  *     after 5 ms without work and is launched again by the next request;
  *     while it runs, those SMs are busy polling, so other kernels of the
- *     process get the remaining SMs;
+ *     process get the remaining SMs.  (With CUDA's lazy module loading, a
+ *     kernel launched for the first time in the process waits for the
+ *     kernels already running: exactsum_server_create therefore loads all
+ *     of this library's kernels; other code that launches a kernel for the
+ *     first time while the resident kernel runs waits until requests pause
+ *     for 5 ms, unless the process loads modules eagerly,
+ *     CUDA_MODULE_LOADING=EAGER);
  *   resident = 0: continuous-batching steps (one kernel launch per step,
  *     carrying a chunk of every express request in flight) on the free SMs
  *     (all SMs while no bulk launch is in flight).

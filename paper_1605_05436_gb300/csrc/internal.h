@@ -25,6 +25,8 @@ struct SumArgs {
 constexpr unsigned long long STATUS_BAD_OFFSETS = 1ull, STATUS_MAP_OVERFLOW = 2ull, STATUS_TIMEOUT = 4ull;
 
 cudaError_t launch_sum(int in_dt, const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out);
+cudaError_t preload_sum_kernels();
+cudaError_t trunc_preload();
 cudaError_t launch_round_acc(const int64_t* acc, int in_dt, int out, int mode, void* result,
                              cudaStream_t stream);
 

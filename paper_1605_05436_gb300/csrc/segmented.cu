@@ -493,6 +493,17 @@ static cudaError_t configure_kernels(int dev) {
   return cudaSuccess;
 }
 
+cudaError_t seg_preload() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = configure_kernels(dev);
+  cudaFuncAttributes at;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&at, (const void*)seg_count_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&at, (const void*)seg_scan_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&at, (const void*)seg_base_kernel);
+  return e;
+}
+
 int seg_warps_choice(int in_dt, int idx) {
   if (idx == 2) return in_dt == F64 ? SegTma<F64>::W : SegTma<F32>::W;
   if (idx == 3) return in_dt == F64 ? WinGeom<F64>::W : WinGeom<F32>::W;

@@ -35,5 +35,7 @@ cudaError_t seg_enqueue(int in_dt, const SegArgs& a, int warps, int kind, int nu
 // Warps per CTA of the reducer for a dtype: register form choice 0 or 1;
 // choice 2 is the TMA form's fixed shape, choice 3 the windowed form's.
 int seg_warps_choice(int in_dt, int idx);
+// Load and configure every segmented kernel on the current device now.
+cudaError_t seg_preload();
 
 }  // namespace es

@@ -45,6 +45,7 @@
 #include "digits.cuh"
 #include "handle.h"
 #include "internal.h"
+#include "segmented.h"
 #include "serve.h"
 
 namespace {
@@ -685,6 +686,13 @@ exactsum_status exactsum_server_create(exactsum_server_t* out, int device, int m
   ok = ok && cudaHostAlloc(&s->h_bulk_res, (size_t)max_slots * sizeof(uint64_t), cudaHostAllocMapped) == cudaSuccess;
   ok = ok && cudaHostGetDevicePointer((void**)&s->d_bulk_res, s->h_bulk_res, 0) == cudaSuccess;
   ok = ok && es::serve_resident_configure() == cudaSuccess;
+  // the library's kernels are loaded now, not at a first launch next to a
+  // running resident kernel (a launch that has to load its module waits
+  // for the kernels already running, and the resident kernel leaves only
+  // when requests pause)
+  ok = ok && es::preload_sum_kernels() == cudaSuccess;
+  ok = ok && es::seg_preload() == cudaSuccess;
+  ok = ok && es::trunc_preload() == cudaSuccess;
   ok = ok && cudaHostAlloc(&s->hq, sizeof(es::XQueue), cudaHostAllocMapped) == cudaSuccess;
   if (ok) std::memset(s->hq, 0, sizeof(es::XQueue));
   ok = ok && cudaHostGetDevicePointer((void**)&s->dq, s->hq, 0) == cudaSuccess;

@@ -735,7 +735,9 @@ static cudaError_t configure_once(const void* fn, size_t smem, std::atomic<bool>
   return cudaSuccess;
 }
 
-static cudaError_t launch_sum_bf16t(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out) {
+// launch = false: only load and configure the kernel (see preload_sum_kernels).
+static cudaError_t launch_sum_bf16t(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out,
+                                    bool launch = true) {
   constexpr int C = ES_BF16T_C, U = ES_BF16T_U, S = ES_BF16T_S;
   constexpr int T = C * 32;
   constexpr size_t DIG_BYTES = ((size_t)FDIG_INT_DIGITS * T * 4 + 127) / 128 * 128;
@@ -743,7 +745,7 @@ static cudaError_t launch_sum_bf16t(const SumArgs& a, int max_ctas, cudaStream_t
   static_assert(SMEM + 2048 <= 232448, "shared memory per CTA");
   static std::atomic<bool> configured[64] = {};  // idempotent set-up; atomic for concurrent first calls
   cudaError_t e = configure_once((const void*)sum_kernel_bf16t<C, U, S>, SMEM, configured);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !launch) return e;
   const int64_t want = (a.nvec + 2 * T - 1) / (2 * T);
   const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
   if (grid_out) *grid_out = grid;
@@ -751,13 +753,14 @@ static cudaError_t launch_sum_bf16t(const SumArgs& a, int max_ctas, cudaStream_t
   return cudaGetLastError();
 }
 
-static cudaError_t launch_sum_bf16f(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out) {
+static cudaError_t launch_sum_bf16f(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out,
+                                    bool launch = true) {
   constexpr int T = ES_BF16F_T, U = ES_BF16F_U;
   constexpr size_t SMEM = (size_t)(ES_BF16F_SETS * FDIG_DIGITS + FDIG_INT_DIGITS) * T * 4;
   static_assert(SMEM + 2048 <= 232448, "shared memory per CTA");
   static std::atomic<bool> configured[64] = {};  // idempotent set-up; atomic for concurrent first calls
   cudaError_t e = configure_once((const void*)sum_kernel_bf16f<T, U>, SMEM, configured);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !launch) return e;
   const int64_t want = (a.nvec + 2 * T - 1) / (2 * T);
   const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
   if (grid_out) *grid_out = grid;
@@ -766,9 +769,10 @@ static cudaError_t launch_sum_bf16f(const SumArgs& a, int max_ctas, cudaStream_t
 }
 
 template <int DT>
-static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out) {
-  if constexpr (DT == BF16 && ES_BF16_FFMA == 2) return launch_sum_bf16t(a, max_ctas, stream, grid_out);
-  if constexpr (DT == BF16 && ES_BF16_FFMA == 1) return launch_sum_bf16f(a, max_ctas, stream, grid_out);
+static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out,
+                                bool launch = true) {
+  if constexpr (DT == BF16 && ES_BF16_FFMA == 2) return launch_sum_bf16t(a, max_ctas, stream, grid_out, launch);
+  if constexpr (DT == BF16 && ES_BF16_FFMA == 1) return launch_sum_bf16f(a, max_ctas, stream, grid_out, launch);
   using Cfg = SumConfig<DT>;
   using D = typename Cfg::Digit;
   constexpr int ND = ColumnDigits<DT, D>::value;
@@ -784,7 +788,7 @@ static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t str
   else fn = (const void*)sum_kernel<DT, Cfg::T, Cfg::U, D>;
   static std::atomic<bool> configured[64] = {};  // idempotent set-up; atomic for concurrent first calls
   cudaError_t e = configure_once(fn, SMEM, configured);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !launch) return e;
   // at least two vectors per column per CTA, at most one CTA per SM
   const int64_t want = (a.nvec + 2 * COLS - 1) / (2 * COLS);
   const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
@@ -794,6 +798,21 @@ static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t str
   else
     sum_kernel<DT, Cfg::T, Cfg::U, D><<<grid, THREADS, SMEM, stream>>>(a);
   return cudaGetLastError();
+}
+
+// Load and configure the single-array kernels of every input format now
+// (setting a kernel's attribute loads a lazily loaded kernel): a first
+// launch that has to load its module waits for the kernels already running,
+// which a caller with a resident kernel on the device must not meet
+// mid-stream.
+cudaError_t preload_sum_kernels() {
+  const SumArgs none{};
+  cudaError_t e = launch_sum_t<F64>(none, 1, nullptr, nullptr, false);
+  if (e == cudaSuccess) e = launch_sum_t<F32>(none, 1, nullptr, nullptr, false);
+  if (e == cudaSuccess) e = launch_sum_t<BF16>(none, 1, nullptr, nullptr, false);
+  cudaFuncAttributes at;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&at, (const void*)round_acc_kernel);
+  return e;
 }
 
 cudaError_t launch_sum(int in_dt, const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out) {

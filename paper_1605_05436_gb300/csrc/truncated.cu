@@ -390,6 +390,21 @@ static cudaError_t launch_trunc_t(const TruncArgs& a, int max_ctas, cudaStream_t
   return cudaGetLastError();
 }
 
+// Load every truncated-pass kernel on the current device now.
+cudaError_t trunc_preload() {
+  cudaFuncAttributes at;
+  const void* fns[] = {(const void*)trunc_sum_kernel<F64, 2>,  (const void*)trunc_sum_kernel<F64, 4>,
+                       (const void*)trunc_sum_kernel<F64, 16>, (const void*)trunc_sum_kernel<F32, 2>,
+                       (const void*)trunc_sum_kernel<F32, 4>,  (const void*)trunc_sum_kernel<F32, 16>,
+                       (const void*)trunc_sum_kernel<BF16, 2>, (const void*)trunc_sum_kernel<BF16, 4>,
+                       (const void*)trunc_sum_kernel<BF16, 16>};
+  for (const void* f : fns) {
+    const cudaError_t e = cudaFuncGetAttributes(&at, f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <int DT>
 static cudaError_t launch_trunc_dt(int R, const TruncArgs& a, int max_ctas, cudaStream_t stream) {
   switch (R) {
