@@ -127,27 +127,33 @@ class ClockSampler:
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sum_kernel_tma_f64_traffic.json")
-KERNEL_SOURCES = ["sum_kernels.cu", "stream.cuh", "digits.cuh", "tma.cuh", "finalize.cuh", "internal.h"]
+KERNEL_SOURCES = ["sum_kernels.cu", "sum_common.cuh", "stream.cuh", "digits.cuh", "tma.cuh", "finalize.cuh",
+                  "internal.h"]
+# the BF16 FP32-digit kernel (narrow block)
+TRAFFIC_FILE_BF16 = os.path.join(ROOT, "profiles", "sum_kernel_bf16t_traffic.json")
+KERNEL_SOURCES_BF16 = ["sum_bf16.cu", "sum_common.cuh", "fdigits.cuh", "stream.cuh", "digits.cuh", "tma.cuh",
+                       "finalize.cuh", "internal.h"]
 
 
-def kernel_source_digest() -> str:
+def kernel_source_digest(sources=None) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in (KERNEL_SOURCES if sources is None else sources):
         with open(os.path.join(ROOT, "paper_1605_05436_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def measured_traffic(n):
-    """DRAM bytes per launch of the FP64 sum kernel from the committed ncu
-    capture, or None when the kernel sources changed since it was taken or
-    the size differs."""
-    if not os.path.exists(TRAFFIC_FILE):
+def measured_traffic(n, record=None, sources=None):
+    """DRAM bytes per launch of a kernel from its committed ncu capture, or
+    None when the kernel sources changed since it was taken or the size
+    differs."""
+    record = TRAFFIC_FILE if record is None else record
+    if not os.path.exists(record):
         return None
-    with open(TRAFFIC_FILE) as fh:
+    with open(record) as fh:
         d = json.load(fh)
-    if d.get("kernel_sources_sha256") != kernel_source_digest() or d.get("n") != n:
+    if d.get("kernel_sources_sha256") != kernel_source_digest(sources) or d.get("n") != n:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -686,6 +692,8 @@ def bench_narrow(es, W, torch, dev, dt, steps, warmup, log2n=None, check=True):
                       "unit": "GB/s", "hbm_frac": round(achieved / peak, 4),
                       "peak_kind": f"{peak_kind} (STREAM-style copy)",
                       "algorithmic_bytes_per_launch": n * eb,
+                      "traffic": (measured_traffic(n, TRAFFIC_FILE_BF16, KERNEL_SOURCES_BF16)
+                                  if dt == es.BF16 else None),
                       "alu_roof_tera_lane_ops_per_s": round(alu_roof / 1e12, 2),
                       "alu_roof": "SMs x 4 sub-partitions x 16 ALU lanes per cycle x median SM clock; "
                                   "instructions per element from ncu are in profiles/"},

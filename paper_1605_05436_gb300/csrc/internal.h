@@ -26,6 +26,9 @@ constexpr unsigned long long STATUS_BAD_OFFSETS = 1ull, STATUS_MAP_OVERFLOW = 2u
 
 cudaError_t launch_sum(int in_dt, const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out);
 cudaError_t preload_sum_kernels();
+// BF16 single-array kernels on FP32 digit columns (sum_bf16.cu); launch =
+// false only loads and configures the kernel.
+cudaError_t launch_sum_bf16(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out, bool launch);
 cudaError_t trunc_preload();
 cudaError_t launch_round_acc(const int64_t* acc, int in_dt, int out, int mode, void* result,
                              cudaStream_t stream);
