@@ -525,6 +525,78 @@ def per_request_baseline(es, torch, dev, ns, dts, offs, arr, base, isz, ring=819
             "_bits": res.cpu().numpy().view(np.uint64)}
 
 
+def serving_isolated_latency(es, W, torch, dev, log2s=(10, 14, 16, 18, 20, 22, 24, 26), reps=200, lanes=None):
+    """Latency of lone FP64 requests (one at a time, 100 us apart, median of
+    `reps`): one exactsum_sum launch with a CUDA event polled from the host,
+    against the serving engine (with the given lanes, else its defaults)."""
+    pool = torch.from_numpy(W.uniform_f64(1 << max(log2s), 0).view(np.int64)).to(dev)
+    base = pool.data_ptr()
+    lib = es.library()
+    h = es.handle_for(dev.index)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    res = torch.zeros(1, dtype=torch.int64, device=dev)
+    ev = torch.cuda.Event()
+
+    def pause():
+        t1 = time.perf_counter_ns()
+        while time.perf_counter_ns() - t1 < 100_000:
+            pass
+
+    rows = []
+    for lg in log2s:
+        n = 1 << lg
+        lat = []
+        for _ in range(reps):
+            t0 = time.perf_counter_ns()
+            lib.exactsum_sum(h, base, n, es.F64, es.F64, es.RNE, res.data_ptr(), sp)
+            ev.record(stream)
+            while not ev.query():
+                pass
+            lat.append(time.perf_counter_ns() - t0)
+            pause()
+        direct = float(np.median(lat)) / 1e3
+        s = es.exactsum_server_create(dev.index, 128, 4 << 30, 1 << 21, 1 << 15, 2)
+        try:
+            if lanes is not None:
+                es.exactsum_server_set_lanes(s, *lanes)
+            lat = []
+            for _ in range(reps):
+                es.exactsum_server_submit(s, base, n, es.F64, es.F64, es.RNE, 0)
+                while True:
+                    got = es.exactsum_server_poll(s, 16)
+                    if got:
+                        break
+                lat.append(got[0].done_ns - got[0].submit_ns)
+                pause()
+        finally:
+            es.exactsum_server_destroy(s)
+        rows.append({"log2n": lg, "one_launch_us": round(direct, 1), "engine_us": round(float(np.median(lat)) / 1e3, 1)})
+    return rows
+
+
+def run_serving(args):
+    """The serving measurement alone, with chosen lanes (profiling runs)."""
+    import torch
+
+    import paper_1605_05436_gb300 as es
+    from paper_1605_05436_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    es.build()
+    lanes = tuple(int(v) for v in args.lanes.split(",")) if args.lanes else None
+    line = {"metric": "served exact sums: latency and throughput (profiling case)",
+            "lanes": args.lanes or "library defaults"}
+    if args.isolated_latency:
+        line["isolated"] = serving_isolated_latency(es, W, torch, dev, lanes=lanes)
+    else:
+        line["serving"] = bench_serving(es, W, torch, dev, args.requests, check=not args.no_check,
+                                        per_request=not args.no_per_request, lanes=lanes)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def bench_adaptive(es, torch, dev, x, n, reps=3):
     """The condition-number-sensitive path (r-truncated passes, r <- r^2)
     beside the exact single pass, on the benchmark input and on a
@@ -710,9 +782,10 @@ def bench_narrow(es, W, torch, dev, dt, steps, warmup, log2n=None, check=True):
     return r
 
 
-# What bounds each narrow-format kernel (from ncu: pipe utilisation and DRAM
-# throughput of the current kernels).
-NARROW_BOUND = {"f32": "alu", "bf16": "alu"}
+# What bounds each narrow-format kernel (from ncu): FP32 keeps the integer ALU
+# pipe 80 % busy; the BF16 FP32-digit kernel leaves it at 67 % and streams at
+# 76-80 % of HBM bandwidth, near issue-bound, so its roof is the HBM one.
+NARROW_BOUND = {"f32": "alu", "bf16": "hbm"}
 
 
 def es_sm_count(torch, dev) -> int:
@@ -947,6 +1020,12 @@ def main():
                     help="skip the one-launch-per-request serving baseline")
     ap.add_argument("--no-narrow", action="store_true", help="skip the FP32/BF16 block of the default line")
     ap.add_argument("--no-delta", action="store_true", help="skip the delta-sweep block of the default line")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="print only the serving measurement (profiling runs)")
+    ap.add_argument("--lanes", default=None,
+                    help="with --serving-only: EXPRESS_MAX_BYTES,EXPRESS_SMS,RESIDENT for exactsum_server_set_lanes")
+    ap.add_argument("--isolated-latency", action="store_true",
+                    help="with --serving-only: lone requests of 2^10..2^26 elements, engine against one launch")
     ap.add_argument("--adaptive", action="store_true",
                     help="also time the condition-number-sensitive path with --primary-only or --log2n")
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64",
@@ -960,6 +1039,8 @@ def main():
         return run_reference(args)
     if args.delta_sweep:
         return run_delta_sweep(args)
+    if args.serving_only:
+        return run_serving(args)
     if args.dtype != "f64":
         return run_narrow(args)
     return run_ours(args)
