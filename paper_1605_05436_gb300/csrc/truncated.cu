@@ -185,7 +185,9 @@ struct Window {
   // Add an element's parts: lo at digit k, hi at digit k + 1.  Fast path:
   // both inside the window (low < k, k + 1 <= top), one unsigned compare.
   // (A separate branch for parts that are both below the window, skipping
-  // the additions, measured slower: the warp then runs three paths.)
+  // the additions, measured slower: the warp then runs three paths; a warp
+  // vote so that all lanes take one path measured 3 % faster on ill-
+  // conditioned input and 6 % slower on well-conditioned input.)
   // Otherwise: move the window up first if a non-zero part lies above it
   // (out of line: rare once the largest magnitudes have been seen), then add
   // without a branch -- a part outside the window adds 0 to the slot its
