@@ -268,3 +268,79 @@ def test_lanes_are_set_before_the_first_request(pools):
         assert collect(server, 1)[rid].result_bits == oracle.exact_sum(bits[:1000], threads=2)
     finally:
         es.exactsum_server_destroy(server)
+
+
+def test_resident_kernel_leaves_when_idle_and_comes_back(pools):
+    """The resident express kernel leaves after 5 ms without requests; the
+    next request launches it again.  Requests spaced 20 ms apart (so the
+    kernel has left before each) and bursts in between are all exact, and
+    the engine counts the relaunches."""
+    bits, dx = pools[es.F64]
+    server = es.exactsum_server_create(0, 32, 1 << 30, 1 << 16, 1 << 12)
+    try:
+        rng = np.random.default_rng(17)
+        want = {}
+        for round_ in range(4):
+            time.sleep(0.02)
+            for k in range(1 + 5 * round_):
+                n = int(rng.integers(1, 1 << 18))
+                o = int(rng.integers(0, len(bits) - n))
+                want[es.exactsum_server_submit(server, dx[o:].data_ptr(), n, es.F64, es.F64, es.RNE, 0)] = (o, n)
+            recs = collect(server, len(want))
+            for rid, (o, n) in want.items():
+                assert recs[rid].status == es.OK
+                assert recs[rid].result_bits == oracle.exact_sum(bits[o:o + n], threads=2), (round_, rid)
+            want.clear()
+        assert es.exactsum_server_stats(server)["steps"] >= 4  # express-lane kernel launches
+    finally:
+        es.exactsum_server_destroy(server)
+
+
+def test_concurrent_submitters(pools):
+    """Four host threads submit at once (the submit call is thread-safe):
+    every request, from either lane, gives the oracle's bits."""
+    import threading
+    server = es.exactsum_server_create(0, 64, 1 << 30, 1 << 16, 1 << 12)
+    try:
+        es.exactsum_server_set_lanes(server, 1 << 19, 8)
+        out = {}
+        lock = threading.Lock()
+
+        def worker(seed):
+            rng = np.random.default_rng(seed)
+            for _ in range(60):
+                dt = [es.F64, es.F32, es.BF16][int(rng.integers(0, 3))]
+                bits, dx = pools[dt]
+                n = int(rng.integers(0, 1 << int(rng.integers(4, 21))))
+                o = int(rng.integers(0, len(bits) - n + 1))
+                rid = es.exactsum_server_submit(server, dx[o:].data_ptr() if n else 0, n, dt, es.F64, es.RNE, 0)
+                with lock:
+                    out[rid] = (dt, o, n)
+
+        threads = [threading.Thread(target=worker, args=(s,)) for s in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        recs = collect(server, len(out))
+        assert len(recs) == len(out) == 240
+        for rid, (dt, o, n) in out.items():
+            assert recs[rid].status == es.OK
+            assert recs[rid].result_bits == oracle.exact_sum(pools[dt][0][o:o + n], dt, es.F64, es.RNE, 2), rid
+    finally:
+        es.exactsum_server_destroy(server)
+
+
+def test_destroy_while_resident_kernel_waits(pools):
+    """Destroying a server right after its requests complete (the resident
+    kernel still polling the queue) stops the kernel and returns; the device
+    then runs other work normally."""
+    bits, dx = pools[es.F64]
+    for _ in range(3):
+        server = es.exactsum_server_create(0, 8, 1 << 30, 1 << 15, 1 << 12)
+        rid = es.exactsum_server_submit(server, dx.data_ptr(), 5000, es.F64, es.F64, es.RNE, 0)
+        assert collect(server, 1)[rid].result_bits == oracle.exact_sum(bits[:5000], threads=2)
+        es.exactsum_server_destroy(server)
+    r = es.exact_sum(dx[:100_000])
+    torch.cuda.synchronize()
+    assert G.result_bits(r, es.F64)[0] == oracle.exact_sum(bits[:100_000], threads=2)
