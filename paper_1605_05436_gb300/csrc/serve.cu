@@ -103,12 +103,13 @@ struct exactsum_server {
   int64_t budget = 0, chunk = 0, tile = 0, max_steps = 0;
   cudaStream_t compute = nullptr, copy = nullptr, bulk = nullptr;
   int64_t* slot_acc = nullptr;
-  // bulk lane: the single-array kernel's workspace (its launches are ordered
-  // on the bulk stream, so one suffices) and per-slot results in pinned,
-  // device-mapped host memory
+  // lanes (exactsum_server_set_lanes), fixed once the first request arrives
   int64_t express_max_bytes = SERVE_EXPRESS_MAX_BYTES;
   int express_sms = SERVE_EXPRESS_SMS;
   std::atomic<bool> started{false};
+  // bulk lane: the single-array kernel's workspace (its launches are ordered
+  // on the bulk stream, so one suffices) and per-slot results in pinned,
+  // device-mapped host memory
   int64_t* bulk_partials = nullptr;
   unsigned int* bulk_ticket = nullptr;
   unsigned long long* bulk_status = nullptr;
@@ -124,7 +125,6 @@ struct exactsum_server {
   unsigned int* x_done = nullptr;           // device, max_slots
   es::ServeDone* h_xres = nullptr;          // max_slots
   es::ServeDone* d_xres = nullptr;
-  unsigned long long* x_status = nullptr;
   int64_t x_next_req = 0;
   std::deque<Req*> x_waiting;               // admitted, not yet published
   int64_t x_launches = 0;
@@ -319,7 +319,6 @@ bool ensure_resident(exactsum_server* s) {
   a.done = s->x_done;
   a.slot_acc = s->slot_acc;
   a.results = s->d_xres;
-  a.status = s->x_status;
   a.idle_ns = SERVE_RESIDENT_IDLE_NS;
   // the oldest request not yet complete: the kernel's warps scan from there
   a.first_req = s->x_next_req;
@@ -640,7 +639,6 @@ void server_free(exactsum_server* s) {
   if (s->h_xres) cudaFreeHost(s->h_xres);
   cudaFree(s->x_tiles);
   cudaFree(s->x_done);
-  cudaFree(s->x_status);
   if (s->compute) cudaStreamDestroy(s->compute);
   if (s->copy) cudaStreamDestroy(s->copy);
   if (s->bulk) cudaStreamDestroy(s->bulk);
@@ -703,8 +701,6 @@ exactsum_status exactsum_server_create(exactsum_server_t* out, int device, int m
   ok = ok && cudaMemset(s->x_tiles, 0, es::XRING * sizeof(unsigned long long)) == cudaSuccess;
   ok = ok && cudaMalloc(&s->x_done, (size_t)max_slots * sizeof(unsigned int)) == cudaSuccess;
   ok = ok && cudaMemset(s->x_done, 0, (size_t)max_slots * sizeof(unsigned int)) == cudaSuccess;
-  ok = ok && cudaMalloc(&s->x_status, sizeof(unsigned long long)) == cudaSuccess;
-  ok = ok && cudaMemset(s->x_status, 0, sizeof(unsigned long long)) == cudaSuccess;
   for (auto& b : s->bufs) {
     ok = ok && cudaMallocHost(&b.h_block, sizeof(es::ServeBlock)) == cudaSuccess;
     ok = ok && cudaHostAlloc(&b.h_done, es::SERVE_MAX_ITEMS * sizeof(es::ServeDone), cudaHostAllocMapped) ==

@@ -91,7 +91,6 @@ struct XArgs {
   unsigned int* done;             // device: per slot, tiles finished of its current request
   int64_t* slot_acc;              // device: per slot accumulator
   ServeDone* results;             // pinned: per slot, result bits then the request index + 1
-  unsigned long long* status;     // device status word
   long long idle_ns;              // a CTA that saw no new request for this long exits
   long long first_req;            // every request before this one is complete
 };
