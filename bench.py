@@ -77,15 +77,16 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 100):
         self.gpu = gpu_index
+        self.period_ms = period_ms
         self.proc = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100", "-i", str(self.gpu)],
+                 "-lms", str(self.period_ms), "-i", str(self.gpu)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -124,6 +125,34 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def sustained_clocks(torch, dev, stream, step, seconds=0.6):
+    """The timed region is milliseconds long, shorter than nvidia-smi's
+    sampling period, so its clock samples mostly see the GPU idle.  This
+    repeats the same step back to back for about `seconds` right after the
+    timed region, sampling clocks and throttle reasons every 50 ms, and
+    reports them with the mean device time per step under that sustained
+    load (untimed for the headline value)."""
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    per = max(a.elapsed_time(b), 0.01)
+    reps = max(10, int(seconds * 1e3 / per))
+    with ClockSampler(dev.index, period_ms=50) as clk:
+        a.record(stream)
+        for _ in range(reps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+    out = clk.summary()
+    out["steps"] = reps
+    out["ms_per_step"] = round(a.elapsed_time(b) / reps, 4)
+    return out
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sum_kernel_tma_f64_traffic.json")
@@ -756,6 +785,8 @@ def bench_narrow(es, W, torch, dev, dt, steps, warmup, log2n=None, check=True):
     achieved = n * eb / (ms * 1e-3) / 1e9
     result_bits = int(out.view(torch.int64).item()) & ((1 << (8 * eb)) - 1)
     clk = clocks.summary()
+    sustained = sustained_clocks(torch, dev, stream, lambda: es.exactsum_sum(
+        h, x.data_ptr(), n, dt, dt, es.RNE, out.data_ptr(), stream.cuda_stream))
     sm_mhz = clk.get("sm_mhz") or 2070.0
     alu_roof = es_sm_count(torch, dev) * ALU_LANES_PER_SM_CYCLE * sm_mhz * 1e6
     r = {"workload": f"{name.upper()} n = 2^{log2n}, wide-exponent recipe (seed 0), rounded to the input format",
@@ -769,7 +800,7 @@ def bench_narrow(es, W, torch, dev, dt, steps, warmup, log2n=None, check=True):
                       "alu_roof_tera_lane_ops_per_s": round(alu_roof / 1e12, 2),
                       "alu_roof": "SMs x 4 sub-partitions x 16 ALU lanes per cycle x median SM clock; "
                                   "instructions per element from ncu are in profiles/"},
-         "clocks": clk, "result_bits": f"{result_bits:#x}"}
+         "clocks": clk, "clocks_sustained": sustained, "result_bits": f"{result_bits:#x}"}
     if check:
         import oracle
         t_chk = time.perf_counter()
@@ -853,7 +884,7 @@ def run_narrow(args):
             "dtype": "int64" if dt == es.F32 else "int32", "data": "synthetic",
             "config": {"workload": r["workload"], "launch": "exactsum_sum, one kernel per step"},
             "roofline": r["roofline"], "gpu_launches": args.steps, "clocks": r["clocks"],
-            "result_bits": r["result_bits"]}
+            "clocks_sustained": r["clocks_sustained"], "result_bits": r["result_bits"]}
     if "gpu_result_equals_oracle" in r:
         line["gpu_result_equals_oracle"] = r["gpu_result_equals_oracle"]
     print(json.dumps(line), flush=True)
@@ -965,6 +996,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks.summary(),
+        "clocks_sustained": sustained_clocks(torch, dev, stream, step),
         "result_bits": f"{result_bits & ((1 << 64) - 1):#018x}",
     }
     if args.log2n != LOG2N:
