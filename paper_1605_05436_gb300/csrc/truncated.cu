@@ -9,8 +9,10 @@
 //      tree).  An element is split into two digit parts; a part above the
 //      window moves the window up (the digits that fall out of the bottom are
 //      dropped), a part below the window is dropped;
-//   2. every dropped item is counted, together with the highest digit index
-//      ever dropped: a dropped element part at digit j is smaller than
+//   2. every non-zero dropped item is counted.  Each lies at a digit at or
+//      below the bottom of its thread's final window (the window only moves
+//      up), maxdrop = the highest such bottom over the threads that dropped
+//      anything; a dropped element part at digit j is smaller than
 //      2^(32j + 52) units, a dropped window digit (regularised first) smaller
 //      than 2^(32j + 32), so the total truncated mass is at most
 //      B = events * 2^(32 * maxdrop + 52) units;
@@ -63,31 +65,27 @@ constexpr int TR_REG_EVERY = 1984;  // digit parts between window regularisation
 
 // An element as two radix-2^32 digit parts: value = lo * 2^(32k) + hi * 2^(32(k+1))
 // units, lo in [0, 2^32], hi in [-2^52, 2^52) (the sign folded as in add_f64_e).
+// E is the element's biased exponent field.
 template <int DT>
-__device__ __forceinline__ void split32(uint64_t bits, int& k, int64_t& lo, int64_t& hi) {
-  uint32_t mlo, mhi, p, neg;
+__device__ __forceinline__ void split32(uint64_t bits, uint32_t E, int& k, int64_t& lo, int64_t& hi) {
+  uint32_t mlo, mhi, neg;
   if constexpr (DT == F64) {
-    const uint32_t l = (uint32_t)bits, h = (uint32_t)(bits >> 32);
-    const uint32_t E = (h >> 20) & 0x7FFu;
-    mlo = l;
+    const uint32_t h = (uint32_t)(bits >> 32);
+    mlo = (uint32_t)bits;
     mhi = (h & 0xFFFFFu) | (E != 0u ? 0x100000u : 0u);
-    p = max(E, 1u) - 1u;
     neg = h >> 31;
   } else if constexpr (DT == F32) {
     const uint32_t w = (uint32_t)bits;
-    const uint32_t E = (w >> 23) & 0xFFu;
     mlo = (w & 0x7FFFFFu) | (E != 0u ? 0x800000u : 0u);
     mhi = 0;
-    p = max(E, 1u) - 1u;
     neg = w >> 31;
   } else {
     const uint32_t w = (uint32_t)bits & 0xFFFFu;
-    const uint32_t E = (w >> 7) & 0xFFu;
     mlo = (w & 0x7Fu) | (E != 0u ? 0x80u : 0u);
     mhi = 0;
-    p = max(E, 1u) - 1u;
     neg = w >> 15;
   }
+  const uint32_t p = max(E, 1u) - 1u;
   const uint32_t sm = 0u - neg;
   const uint32_t xl = mlo ^ sm, xh = mhi ^ sm;
   const uint32_t w0 = __funnelshift_l(sm, xl, p);
@@ -98,19 +96,30 @@ __device__ __forceinline__ void split32(uint64_t bits, int& k, int64_t& lo, int6
   hi = (int64_t)(((uint64_t)w2 << 32) | w1);
 }
 
-// The R-digit window of one thread: digit i (top - R < i <= top) lives in
-// slot i mod R of the thread's column (slot s at col[s * TR_T]).
+// The R-digit window of one thread: slot s (0 <= s < R) holds digit
+// low + 1 + s, top = low + R (slot s at col[s * TR_T]).  Digits at or below
+// `low` are outside the window; `low` never decreases, so every item a
+// thread drops lies at a digit <= its final `low`.
 //
 // The rare window moves are kept out of line (so that the per-element path
 // stays small) and report what they did packed into one 64-bit value:
-// new top | (items dropped) << 16 | (highest dropped digit + 1) << 32.
-template <int R>
-__device__ __forceinline__ int64_t& win_slot(int64_t* col, int i) {
-  return col[(i & (R - 1)) * TR_T];
+// new top | (non-zero digits dropped) << 32.
+__device__ __forceinline__ uint64_t win_pack(int top, uint32_t dropped) {
+  return (uint64_t)(uint32_t)top | ((uint64_t)dropped << 32);
 }
 
-__device__ __forceinline__ uint64_t win_pack(int top, uint32_t dropped, int maxdrop) {
-  return (uint64_t)(uint32_t)top | ((uint64_t)dropped << 16) | ((uint64_t)(uint32_t)(maxdrop + 1) << 32);
+// Move the window up by d >= 1 digits: slots below d leave (counted when
+// non-zero), the rest move down, the top d slots start at zero.
+template <int R>
+__device__ __forceinline__ uint32_t win_shift(int64_t* col, int d) {
+  uint32_t dropped = 0;
+#pragma unroll 1
+  for (int s = 0; s < R; ++s) {
+    int64_t& v = col[s * TR_T];
+    if (s < d && v != 0) ++dropped;
+    v = s + d < R ? col[(s + d) * TR_T] : 0;
+  }
+  return dropped;
 }
 
 // Lemma 1 carries inside the window (balanced digits); a carry out of the
@@ -118,63 +127,49 @@ __device__ __forceinline__ uint64_t win_pack(int top, uint32_t dropped, int maxd
 template <int R>
 __device__ __noinline__ uint64_t win_regularise(int64_t* col, int top) {
   uint32_t dropped = 0;
-  int maxdrop = -1;
   int64_t carry = 0;
-  for (int i = top - R + 1; i <= top; ++i) {
-    const int64_t v = win_slot<R>(col, i) + carry;
+#pragma unroll 1
+  for (int s = 0; s < R; ++s) {
+    const int64_t v = col[s * TR_T] + carry;
     const int64_t c = (v + ((int64_t)1 << 31)) >> 32;
-    win_slot<R>(col, i) = v - (c << 32);
+    col[s * TR_T] = v - (c << 32);
     carry = c;
   }
   if (carry != 0) {
-    int64_t& s = win_slot<R>(col, top + 1);  // holds digit top + 1 - R, now leaving the window
-    if (s != 0) {
-      ++dropped;
-      maxdrop = top + 1 - R;
-    }
-    s = carry;
+    dropped = win_shift<R>(col, 1);
+    col[(R - 1) * TR_T] = carry;
     ++top;
   }
-  return win_pack(top, dropped, maxdrop);
+  return win_pack(top, dropped);
 }
 
 // Move the window up so that its top digit is t (> top), regularising first.
 template <int R>
 __device__ __noinline__ uint64_t win_raise(int64_t* col, int top, int t) {
   const uint64_t rg = win_regularise<R>(col, top);
-  top = (int)(rg & 0xFFFF);
-  uint32_t dropped = (uint32_t)((rg >> 16) & 0xFFFF);
-  int maxdrop = (int)(rg >> 32) - 1;
+  top = (int)(uint32_t)rg;
+  uint32_t dropped = (uint32_t)(rg >> 32);
   if (t > top) {
-    const int lo = t - top >= R ? top - R + 1 : top + 1 - R;
-    const int hi = t - top >= R ? top : t - R;
-    for (int i = lo; i <= hi; ++i) {  // digits leaving the window
-      int64_t& s = win_slot<R>(col, i);
-      if (s != 0) {
-        ++dropped;
-        maxdrop = max(maxdrop, i);
-        s = 0;
-      }
-    }
+    dropped += win_shift<R>(col, t - top < R ? t - top : R);
     top = t;
   }
-  return win_pack(top, dropped, maxdrop);
+  return win_pack(top, dropped);
 }
 
 template <int R>
 struct Window {
   int64_t* col;
   int top;                     // most significant digit held; -1 while empty
-  int low;                     // top - R: digits <= low are outside the window
-  unsigned long long events;   // items dropped
-  int maxdrop;                 // highest digit index dropped; -1 if none
+  int low;                     // top - R
+  unsigned long long events;   // non-zero items dropped
   int adds;                    // parts added since the last regularisation
 
+  __device__ __forceinline__ int64_t& slot(int s) { return col[s * TR_T]; }
+
   __device__ __forceinline__ void absorb(uint64_t r) {
-    top = (int)(r & 0xFFFF);
+    top = (int)(uint32_t)r;
     low = top - R;
-    events += (r >> 16) & 0xFFFF;
-    maxdrop = max(maxdrop, (int)(r >> 32) - 1);
+    events += r >> 32;
   }
 
   __device__ __forceinline__ void regularise() {
@@ -182,23 +177,24 @@ struct Window {
     if (top >= 0) absorb(win_regularise<R>(col, top));
   }
 
-  // Add an element's parts: lo at digit k, hi at digit k + 1.  Fast path:
-  // both inside the window (low < k, k + 1 <= top), one unsigned compare.
-  // (A separate branch for parts that are both below the window, skipping
-  // the additions, measured slower: the warp then runs three paths; a warp
-  // vote so that all lanes take one path measured 3 % faster on ill-
+  // Add an element's parts: lo at digit k, hi at digit k + 1, u = k - low - 1
+  // the slot of the lo part.
+  //  - both inside (0 <= u <= R - 2): two slot additions, one unsigned compare;
+  //  - below (u < 0): the lo part is dropped, and so is the hi part unless
+  //    u = -1 (then it goes to slot 0); non-zero dropped parts are counted;
+  //  - at or above the top: the window moves up first when a non-zero part
+  //    lies above it (out of line: rare once the largest magnitudes have
+  //    been seen); afterwards u is R - 2, or R - 1 with hi = 0.
+  // (A warp vote so that all lanes take one path measured 3 % faster on ill-
   // conditioned input and 6 % slower on well-conditioned input.)
-  // Otherwise: move the window up first if a non-zero part lies above it
-  // (out of line: rare once the largest magnitudes have been seen), then add
-  // without a branch -- a part outside the window adds 0 to the slot its
-  // digit maps to (which changes nothing) and is counted as dropped when
-  // non-zero.  The regularisation counter advances by 2 per element in every
-  // lane alike (a window move regularises too but does not reset it), so
-  // that lanes regularise together.
   __device__ __forceinline__ void add_pair(int k, int64_t lo, int64_t hi) {
-    if ((unsigned)(k - low - 1) <= (unsigned)(R - 2)) {
-      win_slot<R>(col, k) += lo;
-      win_slot<R>(col, k + 1) += hi;
+    int u = k - low - 1;
+    if ((unsigned)u <= (unsigned)(R - 2)) {
+      slot(u) += lo;
+      slot(u + 1) += hi;
+    } else if (u < 0) {
+      if (u == -1) slot(0) += hi;
+      events += (unsigned)(lo != 0) + (unsigned)(u < -1 && hi != 0);
     } else {
       const int t = hi != 0 ? k + 1 : k;
       if (t > top) {
@@ -208,48 +204,70 @@ struct Window {
         } else {
           absorb(win_raise<R>(col, top, t));
         }
+        u = k - low - 1;
       }
-      const bool in_hi = k + 1 > low, in_lo = k > low;
-      win_slot<R>(col, k + 1) += in_hi ? hi : 0;
-      win_slot<R>(col, k) += in_lo ? lo : 0;
-      const bool d_hi = !in_hi && hi != 0, d_lo = !in_lo && lo != 0;
-      events += (unsigned)d_hi + (unsigned)d_lo;
-      maxdrop = max(maxdrop, d_hi ? k + 1 : (d_lo ? k : -1));
+      slot(u) += lo;
+      if (u + 1 < R) slot(u + 1) += hi;
     }
-    adds += 2;
+  }
+
+  // once per vector: every lane counts alike, so that lanes regularise
+  // together (a window move regularises too but does not reset the count)
+  __device__ __forceinline__ void tick(int parts) {
+    adds += parts;
     if (adds >= TR_REG_EVERY) regularise();
   }
 };
 
 template <int DT, int R>
-__device__ __forceinline__ void add_elem(Window<R>& w, uint64_t bits, uint32_t& emax) {
-  constexpr int FB = DT == F64 ? 52 : (DT == F32 ? 23 : 7);
-  constexpr uint64_t EM = (uint64_t)Geometry<DT>::EXP_SPECIAL;
-  emax = max(emax, (uint32_t)((bits >> FB) & EM));
+__device__ __forceinline__ void add_elem(Window<R>& w, uint64_t bits, uint32_t E) {
   int k;
   int64_t lo, hi;
-  split32<DT>(bits, k, lo, hi);
+  split32<DT>(bits, E, k, lo, hi);
   w.add_pair(k, lo, hi);
 }
 
+// All elements of one 16-byte vector; the exponent maximum by three-input
+// maxima, once per two exponents.
 template <int DT, int R>
 __device__ __forceinline__ void add_vec16(Window<R>& w, const uint4& v, uint32_t& emax) {
   if constexpr (DT == F64) {
-    add_elem<DT, R>(w, ((uint64_t)v.y << 32) | v.x, emax);
-    add_elem<DT, R>(w, ((uint64_t)v.w << 32) | v.z, emax);
+    const uint32_t e0 = (v.y >> 20) & 0x7FFu, e1 = (v.w >> 20) & 0x7FFu;
+    emax = __vimax3_u32(emax, e0, e1);
+    add_elem<DT, R>(w, ((uint64_t)v.y << 32) | v.x, e0);
+    add_elem<DT, R>(w, ((uint64_t)v.w << 32) | v.z, e1);
+    w.tick(4);
   } else if constexpr (DT == F32) {
-    add_elem<DT, R>(w, v.x, emax);
-    add_elem<DT, R>(w, v.y, emax);
-    add_elem<DT, R>(w, v.z, emax);
-    add_elem<DT, R>(w, v.w, emax);
+    const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+    uint32_t e[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) e[j] = (q[j] >> 23) & 0xFFu;
+    emax = __vimax3_u32(emax, e[0], e[1]);
+    emax = __vimax3_u32(emax, e[2], e[3]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) add_elem<DT, R>(w, q[j], e[j]);
+    w.tick(8);
   } else {
     const uint32_t q[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      add_elem<DT, R>(w, q[k] & 0xFFFFu, emax);
-      add_elem<DT, R>(w, q[k] >> 16, emax);
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t e0 = (q[j] >> 7) & 0xFFu, e1 = (q[j] >> 23) & 0xFFu;
+      emax = __vimax3_u32(emax, e0, e1);
+      add_elem<DT, R>(w, q[j] & 0xFFFFu, e0);
+      add_elem<DT, R>(w, q[j] >> 16, e1);
     }
+    w.tick(16);
   }
+}
+
+// One element outside the vectors (head or tail).
+template <int DT, int R>
+__device__ __forceinline__ void add_one_elem(Window<R>& w, uint64_t bits, uint32_t& emax) {
+  constexpr int FB = DT == F64 ? 52 : (DT == F32 ? 23 : 7);
+  const uint32_t E = (uint32_t)((bits >> FB) & (uint64_t)Geometry<DT>::EXP_SPECIAL);
+  emax = max(emax, E);
+  add_elem<DT, R>(w, bits, E);
+  w.tick(2);
 }
 
 template <int DT, int R>
@@ -278,7 +296,6 @@ __global__ void __launch_bounds__(TR_T, 1) trunc_sum_kernel(TruncArgs a) {
   w.top = -1;
   w.low = -1 - R;
   w.events = 0;
-  w.maxdrop = -1;
   w.adds = 0;
 #pragma unroll
   for (int s = 0; s < R; ++s) w.col[s * TR_T] = 0;
@@ -312,8 +329,8 @@ __global__ void __launch_bounds__(TR_T, 1) trunc_sum_kernel(TruncArgs a) {
     for (int u = 0; u < TR_U; ++u) add_vec16<DT, R>(w, B[u], emax);
   }
   for (int64_t j = nb * TR_U; j < cnt; ++j) add_vec16<DT, R>(w, ldg_stream(p + j * TR_T), emax);
-  if (blockIdx.x == 0 && t < a.head) add_elem<DT, R>(w, load_one<DT>(a.x, t), emax);
-  if (blockIdx.x == G - 1 && t < a.tail) add_elem<DT, R>(w, load_one<DT>(a.x, a.n - a.tail + t), emax);
+  if (blockIdx.x == 0 && t < a.head) add_one_elem<DT, R>(w, load_one<DT>(a.x, t), emax);
+  if (blockIdx.x == G - 1 && t < a.tail) add_one_elem<DT, R>(w, load_one<DT>(a.x, a.n - a.tail + t), emax);
   w.regularise();
   tops[t] = w.top;
 
@@ -329,15 +346,17 @@ __global__ void __launch_bounds__(TR_T, 1) trunc_sum_kernel(TruncArgs a) {
   }
   __syncthreads();
   if (flags) atomicOr(&blk_flags, flags);
-  if (w.events) atomicAdd(&blk_events, w.events);
-  if (w.maxdrop >= 0) atomicMax(&blk_maxdrop, w.maxdrop);
+  if (w.events) {
+    atomicAdd(&blk_events, w.events);
+    atomicMax(&blk_maxdrop, w.low);  // every dropped item lies at a digit <= low
+  }
 
   // ---- CTA merge: the threads' windows, exactly ----
   for (int i = warp; i < ACC_DIGITS; i += NW) {
     int64_t s = 0;
     for (int j = lane; j < TR_T; j += 32) {
-      const int tp = tops[j];
-      if (tp >= 0 && i <= tp && i > tp - R) s += tr_cols[(i & (R - 1)) * TR_T + j];
+      const int sl = i - tops[j] + R - 1;  // slot of digit i in thread j's window
+      if (tops[j] >= 0 && sl >= 0 && sl < R) s += tr_cols[sl * TR_T + j];
     }
     s = warp_sum(s);
     if (lane == 0) blk[i] = s;
