@@ -49,6 +49,14 @@ __device__ __forceinline__ void store_indexed(void* results, int out, int64_t s,
   store_result((char*)results + s * w, out, bits);
 }
 
+// Round a segment's accumulator into its result slot (one thread), out of
+// line: the windowed reducer's streaming loop runs at 80 registers, and the
+// rounding inlined beside it spills.
+__device__ __noinline__ void round_segment(const SegArgs& a, int64_t s, const int64_t* acc, uint32_t* limbs,
+                                           int in_dt) {
+  store_indexed(a.results, a.out, s, finalize_acc(acc, limbs, in_dt, a.out, a.mode));
+}
+
 __device__ __forceinline__ uint64_t quiet_nan_bits(int out) {
   return out == F64 ? 0x7FF8000000000000ull : (out == F32 ? 0x7FC00000ull : 0x7FC0ull);
 }
@@ -162,16 +170,21 @@ __device__ __forceinline__ TileWork tile_work(const SegArgs& a, int64_t tile) {
 // round the segment at once if this tile is the whole segment, else add it
 // into the segment's accumulator; the warp that retires the last tile of the
 // segment rounds it and clears the accumulator.
-template <int DT, int W>
+// OOL: round through round_segment (out of line) instead of inline.
+template <int DT, int W, bool OOL = false>
 __device__ __forceinline__ void seg_emit(const SegArgs& a, const TileWork& w, int64_t d0, int64_t d1, int64_t d2,
                                          int64_t (*wacc)[ACC_WORDS], uint32_t (*wlimbs)[ACC_DIGITS]) {
+  auto round_into = [&](int64_t s) {
+    if constexpr (OOL) round_segment(a, s, wacc[threadIdx.x >> 5], wlimbs[threadIdx.x >> 5], DT);
+    else store_indexed(a.results, a.out, s, finalize_acc(wacc[threadIdx.x >> 5], wlimbs[threadIdx.x >> 5], DT, a.out, a.mode));
+  };
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (w.ntiles == 1) {
     wacc[warp][lane] = d0;
     wacc[warp][lane + 32] = d1;
     if (lane + 64 < ACC_WORDS) wacc[warp][lane + 64] = d2;
     __syncwarp();
-    if (lane == 0) store_indexed(a.results, a.out, w.s, finalize_acc(wacc[warp], wlimbs[warp], DT, a.out, a.mode));
+    if (lane == 0) round_into(w.s);
     __syncwarp();
   } else {
     unsigned long long* acc = (unsigned long long*)(a.seg_acc + w.s * ACC_WORDS);
@@ -192,7 +205,7 @@ __device__ __forceinline__ void seg_emit(const SegArgs& a, const TileWork& w, in
       acc[lane + 32] = 0;
       if (lane + 64 < ACC_WORDS) acc[lane + 64] = 0;
       __syncwarp();
-      if (lane == 0) store_indexed(a.results, a.out, w.s, finalize_acc(wacc[warp], wlimbs[warp], DT, a.out, a.mode));
+      if (lane == 0) round_into(w.s);
       __syncwarp();
     }
   }
@@ -392,7 +405,7 @@ __global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel_win(SegArgs a) {
     uint32_t flags;
     win_tile<DT, T, U>(a.x, w.lo, w.hi, cols, ov, d0, d1, d2, flags);
     if (lane + 64 >= ACC_DIGITS) d2 = (lane + 64 < ACC_WORDS) ? flag_word(lane + 64, flags, w.hi - w.lo) : 0;
-    seg_emit<DT, W>(a, w, d0, d1, d2, wacc, wlimbs);
+    seg_emit<DT, W, DT == F64>(a, w, d0, d1, d2, wacc, wlimbs);
   }
 }
 
@@ -454,14 +467,14 @@ static cudaError_t set_attr_win_t() {
   using C = WinGeom<DT>;
   static_assert(seg_win_smem<DT>() + (size_t)C::W * (ACC_WORDS * 8 + ACC_DIGITS * 4) <= 232448,
                 "shared memory per CTA");
-  return cudaFuncSetAttribute(seg_sum_kernel_win<DT, C::W, ES_WIN_U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(seg_sum_kernel_win<DT, C::W, C::U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)seg_win_smem<DT>());
 }
 
 template <int DT>
 static void launch_main_win(const SegArgs& a, int grid, cudaStream_t st) {
   using C = WinGeom<DT>;
-  seg_sum_kernel_win<DT, C::W, ES_WIN_U><<<grid, C::W * 32, seg_win_smem<DT>(), st>>>(a);
+  seg_sum_kernel_win<DT, C::W, C::U><<<grid, C::W * 32, seg_win_smem<DT>(), st>>>(a);
 }
 
 template <int DT>

@@ -22,16 +22,18 @@
 
 namespace es {
 
+// Reducer shape per format: WD window digits per lane, W warps per CTA, U
+// 16-byte vectors per lane per batch (two batches in flight).
 #ifndef ES_WIN_F64_W
-#define ES_WIN_F64_W 16
+#define ES_WIN_F64_W 24
 #endif
-#ifndef ES_WIN_U
-#define ES_WIN_U 4
+#ifndef ES_WIN_F64_U
+#define ES_WIN_F64_U 4
 #endif
 template <int DT> struct WinGeom;
-template <> struct WinGeom<F64> { static constexpr int WD = 4, W = ES_WIN_F64_W; };
-template <> struct WinGeom<F32> { static constexpr int WD = 8, W = 16; };
-template <> struct WinGeom<BF16> { static constexpr int WD = 8, W = 16; };
+template <> struct WinGeom<F64> { static constexpr int WD = 4, W = ES_WIN_F64_W, U = ES_WIN_F64_U; };
+template <> struct WinGeom<F32> { static constexpr int WD = 8, W = 16, U = 4; };
+template <> struct WinGeom<BF16> { static constexpr int WD = 8, W = 16, U = 4; };
 
 // Overflow adds per warp between regularisations of an FP64 overflow
 // accumulator: each add changes a digit by at most 2^52, and a check comes
@@ -67,6 +69,19 @@ __device__ __forceinline__ void win_decode(uint64_t bits, int& d, int64_t& lo, i
     lo = (int64_t)(((int32_t)(m << (p & 7u)) ^ sg) - sg);
     hi = 0;
     d = (int)(p >> 3);
+  }
+}
+
+// Biased exponent field and native-radix digit index only (the window
+// base scan needs no parts).
+template <int DT>
+__device__ __forceinline__ void win_digit(uint64_t bits, int& d, uint32_t& E) {
+  if constexpr (DT == F64) {
+    E = (uint32_t)(bits >> 52) & 0x7FFu;
+    d = (int)((max(E, 1u) - 1u) >> 5);
+  } else {
+    E = ((uint32_t)bits >> (DT == F32 ? 23 : 7)) & 0xFFu;
+    d = (int)((max(E, 1u) - 1u) >> 3);
   }
 }
 
@@ -118,8 +133,8 @@ __device__ __forceinline__ void win_tile(const void* x, int64_t elo, int64_t ehi
   uint32_t etop = 0;
   {
     auto top_e = [&](uint64_t bits) {
-      int d; int64_t lo, hi; uint32_t E;
-      decode(bits, d, lo, hi, E);
+      int d; uint32_t E;
+      win_digit<DT>(bits, d, E);
       if (E != Geometry<DT>::EXP_SPECIAL) etop = max(etop, (uint32_t)d + 1u);
     };
     if (nb > 0) {
