@@ -52,6 +52,16 @@ namespace es {
 #ifndef ES_BF16T_S
 #define ES_BF16T_S 2
 #endif
+// Digit stride of the TMA form's columns: the consumer count rounded up to a
+// multiple of 256 (ES_BF16T_PAD = 1), so that a digit's byte offset is the
+// element's masked exponent bits times a constant (one multiply-add; see
+// fdig_add_pair), or the consumer count itself (ES_BF16T_PAD = 0).
+#ifndef ES_BF16T_PAD
+#define ES_BF16T_PAD 1
+#endif
+__host__ __device__ constexpr int bf16t_stride(int consumer_warps) {
+  return ES_BF16T_PAD ? (consumer_warps * 32 + 255) / 256 * 256 : consumer_warps * 32;
+}
 
 // BF16 with FP32 digit columns (fdigits.cuh): every thread owns 32 FP32
 // digits, added by one FFMA per element, and 33 int32 digits that take the
@@ -187,7 +197,8 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
   constexpr int EPB = U * 8;         // elements per consumer thread per stage
   constexpr int FLUSH_BATCHES = (FDIG_MAX_ADDS - 2) / EPB;
   static_assert(FLUSH_BATCHES >= 1, "stage too large for the FP32 digits");
-  constexpr size_t DIG_BYTES = ((size_t)FDIG_INT_DIGITS * T * 4 + 127) / 128 * 128;
+  constexpr int FS = bf16t_stride(C);  // digit stride of the columns, in 4-byte words
+  constexpr size_t DIG_BYTES = ((size_t)FDIG_INT_DIGITS * FS * 4 + 127) / 128 * 128;
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* fd = reinterpret_cast<float*>(smem_raw);                              // 32 (33) x T
@@ -213,7 +224,8 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
     blk_flags = 0;
     mbar_init_fence();
   }
-  for (int i = t; i < FDIG_DIGITS * T; i += NW * 32) fd[i] = 0.0f;
+  // (columns T .. FS - 1 are padding: they stay zero, also for the CTA merge)
+  for (int i = t; i < FDIG_INT_DIGITS * FS; i += NW * 32) fd[i] = 0.0f;
   __syncthreads();
 
   uint32_t flags = 0;
@@ -246,14 +258,14 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
 #if ES_BF16T_WARPFLUSH
     int64_t wd = 0;  // digit `lane` of this warp's int64 accumulator
     float* wcols = fd + warp * 32;
-    auto flush = [&]() { fdig_flush_warp<T>(wcols, lane, wd, spec); };
+    auto flush = [&]() { fdig_flush_warp<FS>(wcols, lane, wd, spec); };
 #else
     int32_t I[FDIG_INT_DIGITS];
 #pragma unroll
     for (int i = 0; i < FDIG_INT_DIGITS; ++i) I[i] = 0;
     int flushes = 0;
     auto flush = [&]() {
-      fdig_flush_regs<T>(fc, I, spec);
+      fdig_flush_regs<FS>(fc, I, spec);
       if (++flushes == FDIG_REG_FLUSHES) {
         fdig_regularise_regs(I);
         flushes = 0;
@@ -277,7 +289,7 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
 #pragma unroll
-        for (int u = 0; u < U; ++u) fdig_add_vec<T>(fc, r[u]);
+        for (int u = 0; u < U; ++u) fdig_add_vec<FS>(fc, r[u]);
       } else {
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -286,7 +298,7 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
         if (lane == 0) mbar_arrive(&empty[s]);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (t + u * T < nv) fdig_add_vec<T>(fc, r[u]);
+          if (t + u * T < nv) fdig_add_vec<FS>(fc, r[u]);
       }
       if (++since_flush == FLUSH_BATCHES) {
         flush();
@@ -294,8 +306,8 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
       }
     }
     if (!ok && lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
-    if (blockIdx.x == 0 && t < a.head) fdig_add_one<T>(fc, (uint32_t)load_one<BF16>(a.x, t));
-    if (blockIdx.x == G - 1 && t < a.tail) fdig_add_one<T>(fc, (uint32_t)load_one<BF16>(a.x, a.n - a.tail + t));
+    if (blockIdx.x == 0 && t < a.head) fdig_add_one<FS>(fc, (uint32_t)load_one<BF16>(a.x, t));
+    if (blockIdx.x == G - 1 && t < a.tail) fdig_add_one<FS>(fc, (uint32_t)load_one<BF16>(a.x, a.n - a.tail + t));
     flush();
 #if ES_BF16T_WARPFLUSH
     // specials and all-zero digits are judged per warp (the flags only
@@ -317,7 +329,7 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
     // the int32 digits take the place of the FP32 digits for the CTA merge
     int32_t* ic = reinterpret_cast<int32_t*>(fd) + t;
 #pragma unroll
-    for (int i = 0; i < FDIG_INT_DIGITS; ++i) ic[i * T] = I[i];
+    for (int i = 0; i < FDIG_INT_DIGITS; ++i) ic[i * FS] = I[i];
 #endif
 #if ES_BF16T_WARPFLUSH
     warp_digit = wd;
@@ -334,10 +346,10 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
     if (lane == 0) wcol[32 * C + warp] = 0;
   }
   __syncthreads();
-  finish_cta<BF16, C, NW, int64_t, true, (size_t)FDIG_DIGITS * T * 4>(a, wcol, blk, limbs, blk_flags, &is_last);
+  finish_cta<BF16, C, NW, int64_t, true, (size_t)FDIG_DIGITS * FS * 4>(a, wcol, blk, limbs, blk_flags, &is_last);
 #else
   __syncthreads();
-  finish_cta<BF16, T, NW, int32_t, true>(a, reinterpret_cast<int32_t*>(fd), blk, limbs, blk_flags, &is_last);
+  finish_cta<BF16, FS, NW, int32_t, true>(a, reinterpret_cast<int32_t*>(fd), blk, limbs, blk_flags, &is_last);
 #endif
 }
 
@@ -346,7 +358,7 @@ static cudaError_t launch_sum_bf16t(const SumArgs& a, int max_ctas, cudaStream_t
                                     bool launch = true) {
   constexpr int C = ES_BF16T_C, U = ES_BF16T_U, S = ES_BF16T_S;
   constexpr int T = C * 32;
-  constexpr size_t DIG_BYTES = ((size_t)FDIG_INT_DIGITS * T * 4 + 127) / 128 * 128;
+  constexpr size_t DIG_BYTES = ((size_t)FDIG_INT_DIGITS * bf16t_stride(C) * 4 + 127) / 128 * 128;
   constexpr size_t SMEM = DIG_BYTES + (size_t)S * T * U * 16 + 2 * S * 8;
   static_assert(SMEM + 2048 <= 232448, "shared memory per CTA");
   static std::atomic<bool> configured[64] = {};  // idempotent set-up; atomic for concurrent first calls
