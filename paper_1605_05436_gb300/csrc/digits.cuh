@@ -470,6 +470,103 @@ __device__ __forceinline__ int64_t digit32(const uint32_t* __restrict__ col, int
   return v;
 }
 
+#ifndef ES_F32_R32
+#define ES_F32_R32 1
+#endif
+#if ES_F32_R32
+// ---------------------------------------------------------------------------
+// FP32 with radix-2^32 sign-split columns (uint64_t digits): an element adds
+// m << (p & 31) (< 2^55, whole, no split) into digit (p >> 5) of its half
+// (positive and negative elements in separate halves, so no sign
+// arithmetic).  Digits overlap: each holds up to 64 bits, and a
+// regularisation (every F32_R32_REG_EVERY additions) moves everything above
+// bit 32 into the next digit.  8 digits take elements (p >> 5 <= 7), two
+// more take carries (the sum of n elements is below 2^(277 + log2 n)), so
+// the two halves take 160 B per thread.  The shift amount is the packed
+// exponent word as it is: a funnel shift uses its low five bits, p & 31.
+// ---------------------------------------------------------------------------
+constexpr int F32_R32_DIGITS = 10;
+// after a regularisation every digit is below 2^32; with at most 511 more
+// additions of less than 2^55 it stays below 2^64 (the callers check after
+// each batch of at most 64 additions, plus a few scalar ones)
+constexpr int F32_R32_REG_EVERY = 400;
+template <>
+struct ColumnDigits<F32, uint64_t> {
+  static constexpr int value = 2 * F32_R32_DIGITS;
+};
+
+template <int STRIDE>
+__device__ __forceinline__ void add_f32_r32(uint64_t* __restrict__ col, uint32_t w, uint32_t E) {
+  const uint32_t m = (w & 0x7FFFFFu) | (E != 0u ? 0x800000u : 0u);
+  const uint32_t p = max(E, 1u) - 1u;
+  col[((p >> 5) + (w >> 31) * (uint32_t)F32_R32_DIGITS) * STRIDE] += (uint64_t)m << (p & 31u);
+}
+
+// Two FP32 elements decoded together in 16-bit halves, as in the radix-2^16
+// form below; m << (p & 31) as two funnel shifts of m by the packed word
+// (the lower element's shift: its low five bits; the upper one's: the word
+// shifted down by 16).
+template <int STRIDE>
+__device__ __forceinline__ void add_f32_r32_pair(uint64_t* __restrict__ col, uint32_t w0, uint32_t w1,
+                                                 uint32_t& emax2) {
+  const uint32_t hh = __byte_perm(w0, w1, 0x7632);      // (w0 >> 16) | (w1 & 0xFFFF0000)
+  const uint32_t E2 = (hh >> 7) & 0x00FF00FFu;          // E of w0 in bits 0-7, of w1 in bits 16-23
+  emax2 = __vimax3_u16x2(emax2, E2, E2);
+  const uint32_t p2 = __viaddmax_s16x2(E2, 0xFFFFFFFFu, 0u);       // max(E - 1, 0) per half
+  const uint32_t hb2 = __vimin3_u16x2(E2, 0x00010001u, 0x00010001u);  // E >= 1 per half
+  // digit p >> 5 of the element's half (negative elements: + F32_R32_DIGITS)
+  const uint32_t q2 = ((p2 >> 5) & 0x00070007u) + ((hh >> 15) & 0x00010001u) * (uint32_t)F32_R32_DIGITS;
+  const uint32_t m0 = (w0 & 0x7FFFFFu) | (hb2 << 23);
+  const uint32_t m1 = (w1 & 0x7FFFFFu) | ((hb2 << 7) & 0x800000u);
+  const uint32_t p1 = p2 >> 16;
+  const uint64_t v0 = ((uint64_t)__funnelshift_l(m0, 0u, p2) << 32) | __funnelshift_l(0u, m0, p2);
+  const uint64_t v1 = ((uint64_t)__funnelshift_l(m1, 0u, p1) << 32) | __funnelshift_l(0u, m1, p1);
+  col[(q2 & 0xFFFFu) * STRIDE] += v0;
+  col[(q2 >> 16) * STRIDE] += v1;
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_vec(uint64_t* __restrict__ col, const uint4& v, uint32_t& emax) {
+  static_assert(DT == F32, "radix-2^32 split columns hold FP32 sums only");
+  add_f32_r32_pair<STRIDE>(col, v.x, v.y, emax);
+  add_f32_r32_pair<STRIDE>(col, v.z, v.w, emax);
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void add_one(uint64_t* __restrict__ col, uint64_t bits, uint32_t& emax) {
+  static_assert(DT == F32, "radix-2^32 split columns hold FP32 sums only");
+  const uint32_t w = (uint32_t)bits;
+  const uint32_t E = (w >> 23) & 0xFFu;
+  emax = max(emax, E);
+  add_f32_r32<STRIDE>(col, w, E);
+}
+
+template <int DT, int STRIDE>
+__device__ __forceinline__ void regularise(uint64_t* __restrict__ col) {
+  static_assert(DT == F32, "radix-2^32 split columns hold FP32 sums only");
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint64_t* c = col + h * F32_R32_DIGITS * STRIDE;
+    uint64_t carry = 0;
+#pragma unroll 3
+    for (int i = 0; i < F32_R32_DIGITS - 1; ++i) {
+      const uint64_t v = c[i * STRIDE];
+      const uint64_t lo = (v & 0xFFFFFFFFu) + carry;  // below 2^33
+      c[i * STRIDE] = lo & 0xFFFFFFFFu;
+      carry = (v >> 32) + (lo >> 32);
+    }
+    c[(F32_R32_DIGITS - 1) * STRIDE] += carry;
+  }
+}
+
+// radix-2^32 digit i: positive half minus negative half
+template <int DT, int STRIDE>
+__device__ __forceinline__ int64_t digit32(const uint64_t* __restrict__ col, int i) {
+  static_assert(DT == F32, "radix-2^32 split columns hold FP32 sums only");
+  if (i >= F32_R32_DIGITS) return 0;
+  return (int64_t)col[i * STRIDE] - (int64_t)col[(F32_R32_DIGITS + i) * STRIDE];
+}
+#else
 // ---------------------------------------------------------------------------
 // FP32 with radix-2^16 sign-split columns (uint64_t digits): 18 digits per
 // half cover the 277-bit range, so the two halves (positive and negative
@@ -561,6 +658,8 @@ __device__ __forceinline__ int64_t digit32(const uint64_t* __restrict__ col, int
   return v;
 }
 
+#endif  // ES_F32_R32
+
 // The exponent maximum as add_vec leaves it: one value, or for the FP32
 // radix-2^16 columns and the BF16 sign-split columns (pair-decoded) two
 // 16-bit maxima packed in one word.
@@ -588,7 +687,11 @@ struct RegEvery<BF16, uint32_t> {
 };
 template <>
 struct RegEvery<F32, uint64_t> {
+#if ES_F32_R32
+  static constexpr int value = F32_R32_REG_EVERY;
+#else
   static constexpr int value = 1 << 24;  // 2^16 + 2^24 * 2^39 < 2^64
+#endif
 };
 
 // Classify one element for the special-value and signed-zero counters.
