@@ -158,6 +158,8 @@ def sustained_clocks(torch, dev, stream, step, seconds=0.6):
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sum_kernel_tma_f64_traffic.json")
 KERNEL_SOURCES = ["sum_kernels.cu", "sum_common.cuh", "stream.cuh", "digits.cuh", "tma.cuh", "finalize.cuh",
                   "internal.h"]
+# the FP32 kernel (narrow block): the same sources as the FP64 one
+TRAFFIC_FILE_F32 = os.path.join(ROOT, "profiles", "sum_kernel_f32_traffic.json")
 # the BF16 FP32-digit kernel (narrow block)
 TRAFFIC_FILE_BF16 = os.path.join(ROOT, "profiles", "sum_kernel_bf16t_traffic.json")
 KERNEL_SOURCES_BF16 = ["sum_bf16.cu", "sum_common.cuh", "fdigits.cuh", "stream.cuh", "digits.cuh", "tma.cuh",
@@ -796,7 +798,7 @@ def bench_narrow(es, W, torch, dev, dt, steps, warmup, log2n=None, check=True):
                       "peak_kind": f"{peak_kind} (STREAM-style copy)",
                       "algorithmic_bytes_per_launch": n * eb,
                       "traffic": (measured_traffic(n, TRAFFIC_FILE_BF16, KERNEL_SOURCES_BF16)
-                                  if dt == es.BF16 else None),
+                                  if dt == es.BF16 else measured_traffic(n, TRAFFIC_FILE_F32, KERNEL_SOURCES)),
                       "alu_roof_tera_lane_ops_per_s": round(alu_roof / 1e12, 2),
                       "alu_roof": "SMs x 4 sub-partitions x 16 ALU lanes per cycle x median SM clock; "
                                   "instructions per element from ncu are in profiles/"},
@@ -823,7 +825,7 @@ def bench_narrow(es, W, torch, dev, dt, steps, warmup, log2n=None, check=True):
 
 
 # What bounds each narrow-format kernel (from ncu): FP32 keeps the integer ALU
-# pipe 80 % busy; the BF16 FP32-digit kernel leaves it at 63 % and streams at
+# pipe 82 % busy; the BF16 FP32-digit kernel leaves it at 63 % and streams at
 # 81 % of HBM bandwidth, near issue-bound, so its roof is the HBM one.
 NARROW_BOUND = {"f32": "alu", "bf16": "hbm"}
 
