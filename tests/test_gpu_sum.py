@@ -125,6 +125,7 @@ def _constant_device(bits_value: int, n: int, dt: int):
 
 
 @pytest.mark.parametrize("dt,n,E", [(es.F64, (1 << 27) + 3, 1024), (es.F32, (1 << 28) + 5, 8),
+                                    (es.F32, (1 << 28) + 5, 32), (es.F32, (1 << 28) + 5, 254),
                                     (es.BF16, (1 << 34) + 7, 8), (es.BF16, (1 << 34) + 7, 15),
                                     (es.BF16, (1 << 30) + 7, 254)])
 def test_regularisation_bound(dt, n, E):
@@ -133,8 +134,11 @@ def test_regularisation_bound(dt, n, E):
     largest in-digit offset), all positive, all negative, and then with
     alternating signs.  n is large enough that each thread regularises
     mid-stream.  The exact sums are closed forms (n * x, -n * x and x),
-    rounded by the oracle.  For FP64 and FP32 the largest offset is
-    p = E - 1 with p mod 32 = 31 or p mod 8 = 7; for BF16 both the integer
+    rounded by the oracle.  For FP64 the largest offset is p = E - 1 with
+    p mod 32 = 31; for FP32 both p mod 32 = 31 (E = 32: the radix-2^32
+    columns, where each addition adds just under 2^55 to one 64-bit digit)
+    and p mod 8 = 7 (E = 8), and the largest finite FP32 (E = 254, whose
+    carries reach the top digit); for BF16 both the integer
     digits' worst case (p mod 8 = 7, E = 8) and the FP32 digits' worst case
     (E mod 8 = 7, E = 15: each addition adds 255 units of 2^-7 to one FP32
     digit, the most an addition can) are run, and the largest finite BF16
@@ -142,7 +146,7 @@ def test_regularisation_bound(dt, n, E):
     if dt == es.F64:
         v, unit, m = (E << 52) | ((1 << 52) - 1), -1074, (1 << 53) - 1   # p = 32*31 + 31
     elif dt == es.F32:
-        v, unit, m = (E << 23) | 0x7FFFFF, -149, (1 << 24) - 1            # p & 7 == 7
+        v, unit, m = (E << 23) | 0x7FFFFF, -149, (1 << 24) - 1            # mantissa all ones
     else:
         v, unit, m = (E << 7) | 0x7F, -133, (1 << 8) - 1
     p = E - 1
