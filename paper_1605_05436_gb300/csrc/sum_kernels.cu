@@ -82,17 +82,20 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
 // the ring, release the stage at once and add the elements into their
 // digit columns.  The bytes in flight live in shared memory rather than in
 // registers, so a CTA keeps S stages of the input in flight.
-template <int DT, int C, int U, int S>
+// D: the digit type of the columns (int64 for FP64; the FP32 radix-2^32
+// sign-split uint64 columns), 8 bytes either way.
+template <int DT, int C, int U, int S, typename D = int64_t>
 __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_tma(SumArgs a) {
+  static_assert(sizeof(D) == 8, "8-byte digits");
   constexpr int T = C * 32;          // consumer threads (digit columns)
   constexpr int NW = C + 1;
-  constexpr int ND = Geometry<DT>::DIGITS;
-  constexpr int REG_EVERY = Geometry<DT>::REG_EVERY;
+  constexpr int ND = ColumnDigits<DT, D>::value;
+  constexpr int REG_EVERY = RegEvery<DT, D>::value;
   constexpr int EPV = 16 / Geometry<DT>::ELEM_BYTES;
   constexpr int BATCH = T * U;       // vectors per stage
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  int64_t* digits = reinterpret_cast<int64_t*>(smem_raw);                       // ND x T
+  D* digits = reinterpret_cast<D*>(smem_raw);                                    // ND x T
   uint4* ring = reinterpret_cast<uint4*>(smem_raw + (size_t)ND * T * 8);        // S x BATCH
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)S * BATCH);       // S
   uint64_t* empty = full + S;                                                    // S
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_tma(SumArgs a) {
     }
   } else {
     // ---- consumers ----
-    int64_t* col = digits + t;
+    D* col = digits + t;
 #pragma unroll 4
     for (int i = 0; i < ND; ++i) col[i * T] = 0;
     uint32_t emax = 0;
@@ -180,6 +183,7 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_tma(SumArgs a) {
       }
     }
     if (!ok && lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
+    emax = emax_unpack<DT, D>(emax);
     if (blockIdx.x == 0 && t < a.head) add_one<DT, T>(col, load_one<DT>(a.x, t), emax);
     if (blockIdx.x == G - 1 && t < a.tail) add_one<DT, T>(col, load_one<DT>(a.x, a.n - a.tail + t), emax);
     regularise<DT, T>(col);
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_tma(SumArgs a) {
   __syncthreads();
   if (flags) atomicOr(&blk_flags, flags);
   __syncthreads();
-  finish_cta<DT, T, NW, int64_t>(a, digits, blk, limbs, blk_flags, &is_last);
+  finish_cta<DT, T, NW, D>(a, digits, blk, limbs, blk_flags, &is_last);
 }
 
 // Round a caller-held accumulator (one thread).
@@ -319,7 +323,7 @@ static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t str
   static_assert(!Cfg::TMA || ((size_t)ND * COLS * 8) % 128 == 0, "ring must start 128-byte aligned");
   static_assert(SMEM + 1024 <= 232448, "shared memory per CTA");
   const void* fn;
-  if constexpr (Cfg::TMA) fn = (const void*)sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S>;
+  if constexpr (Cfg::TMA) fn = (const void*)sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S, D>;
   else fn = (const void*)sum_kernel<DT, Cfg::T, Cfg::U, D>;
   static std::atomic<bool> configured[64] = {};  // idempotent set-up; atomic for concurrent first calls
   cudaError_t e = configure_once(fn, SMEM, configured);
@@ -329,7 +333,7 @@ static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t str
   const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
   if (grid_out) *grid_out = grid;
   if constexpr (Cfg::TMA)
-    sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S><<<grid, THREADS, SMEM, stream>>>(a);
+    sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S, D><<<grid, THREADS, SMEM, stream>>>(a);
   else
     sum_kernel<DT, Cfg::T, Cfg::U, D><<<grid, THREADS, SMEM, stream>>>(a);
   return cudaGetLastError();
