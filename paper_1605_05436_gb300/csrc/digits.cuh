@@ -22,8 +22,9 @@
 //
 // The single-array FP32 and BF16 kernels use sign-split unsigned columns
 // instead (positive and negative elements in separate halves, so an element
-// needs no sign arithmetic): FP32 radix 2^16 in 64-bit digits, BF16 radix
-// 2^8 in 32-bit digits, each defined below with its decode.
+// needs no sign arithmetic): FP32 radix 2^32 in overlapping 64-bit digits
+// (radix 2^16 selectable), BF16 radix 2^8 in 32-bit digits, each defined
+// below with its decode.
 //
 // Regularisation (Lemma 1, generalised to deferred carries): a digit D is
 // replaced by D - c * R and its upper neighbour gains c, with
@@ -661,7 +662,7 @@ __device__ __forceinline__ int64_t digit32(const uint64_t* __restrict__ col, int
 #endif  // ES_F32_R32
 
 // The exponent maximum as add_vec leaves it: one value, or for the FP32
-// radix-2^16 columns and the BF16 sign-split columns (pair-decoded) two
+// sign-split columns and the BF16 sign-split columns (pair-decoded) two
 // 16-bit maxima packed in one word.
 template <int DT, typename D>
 __device__ __forceinline__ uint32_t emax_unpack(uint32_t e) {

@@ -216,9 +216,9 @@ struct SumConfig;
 // Streaming form and shape per input format (chosen by measurement):
 //   TMA = 1: sum_kernel_tma<DT, C, TU, S>, (C + 1) warps, S stages of C*32*TU vectors;
 //   TMA = 0: sum_kernel<DT, T, U>, T threads, U vectors per batch.
-// Digit columns: int64 for FP64; for FP32 radix-2^16 sign-split unsigned
-// 64-bit halves (ES_F32_R16 = 1: radix 2^32 with ES_F32_R32 = 1, else radix
-// 2^16; ES_F32_R16 = 0: radix-2^8 int64); for BF16 sign-split
+// Digit columns: int64 for FP64; for FP32 sign-split unsigned 64-bit halves
+// (ES_F32_R16 = 1: radix 2^32 with ES_F32_R32 = 1, else radix 2^16;
+// ES_F32_R16 = 0: radix-2^8 int64); for BF16 sign-split
 // unsigned 32-bit halves (ES_BF16_SPLIT = 1), else signed int32
 // (ES_BF16_I32 = 1) or int64.
 #ifndef ES_F64_TMA
