@@ -50,8 +50,8 @@ __device__ __forceinline__ void store_indexed(void* results, int out, int64_t s,
 }
 
 // Round a segment's accumulator into its result slot (one thread), out of
-// line: the windowed reducer's streaming loop runs at 80 registers, and the
-// rounding inlined beside it spills.
+// line: the windowed reducer's streaming loop runs at 80 registers or fewer
+// (24-32 warps), and the rounding inlined beside it spills.
 __device__ __noinline__ void round_segment(const SegArgs& a, int64_t s, const int64_t* acc, uint32_t* limbs,
                                            int in_dt) {
   store_indexed(a.results, a.out, s, finalize_acc(acc, limbs, in_dt, a.out, a.mode));
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(W * 32, 1) seg_sum_kernel_win(SegArgs a) {
     uint32_t flags;
     win_tile<DT, T, U>(a.x, w.lo, w.hi, cols, ov, d0, d1, d2, flags);
     if (lane + 64 >= ACC_DIGITS) d2 = (lane + 64 < ACC_WORDS) ? flag_word(lane + 64, flags, w.hi - w.lo) : 0;
-    seg_emit<DT, W, DT == F64>(a, w, d0, d1, d2, wacc, wlimbs);
+    seg_emit<DT, W, true>(a, w, d0, d1, d2, wacc, wlimbs);
   }
 }
 

@@ -32,8 +32,14 @@ namespace es {
 #endif
 template <int DT> struct WinGeom;
 template <> struct WinGeom<F64> { static constexpr int WD = 4, W = ES_WIN_F64_W, U = ES_WIN_F64_U; };
-template <> struct WinGeom<F32> { static constexpr int WD = 8, W = 16, U = 4; };
-template <> struct WinGeom<BF16> { static constexpr int WD = 8, W = 16, U = 4; };
+#ifndef ES_WIN_N_W
+#define ES_WIN_N_W 32
+#endif
+#ifndef ES_WIN_N_U
+#define ES_WIN_N_U 2
+#endif
+template <> struct WinGeom<F32> { static constexpr int WD = 8, W = ES_WIN_N_W, U = ES_WIN_N_U; };
+template <> struct WinGeom<BF16> { static constexpr int WD = 8, W = ES_WIN_N_W, U = ES_WIN_N_U; };
 
 // Overflow adds per warp between regularisations of an FP64 overflow
 // accumulator: each add changes a digit by at most 2^52, and a check comes

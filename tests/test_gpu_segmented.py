@@ -147,7 +147,7 @@ def test_autotune_and_tuning_file(tmp_path):
     s = torch.cuda.current_stream().cuda_stream
     warps, kind, tile, ms = es.exactsum_segmented_autotune(h, x.data_ptr(), d_off.data_ptr(), len(lengths),
                                                            es.F64, scratch.data_ptr(), s)
-    assert warps in (8, 12, 16, 24) and kind in (0, 1, 2) and tile > 0 and ms > 0
+    assert warps in (8, 12, 16, 24, 32) and kind in (0, 1, 2) and tile > 0 and ms > 0
     p = str(tmp_path / "tuning.json")
     es.exactsum_tuning_save(h, p)
     text = open(p).read()
@@ -210,7 +210,7 @@ REDUCERS = {1: "tma", 2: "window"}
 def _force_reducer(h, tmp_path, dt, S, kind, tile):
     lg = int(np.ceil(np.log2(S)))
     # the warps field must name the shape the library is built with
-    warps = {1: 8 if dt == es.F64 else 12, 2: 24 if dt == es.F64 else 16}[kind]
+    warps = {1: 8 if dt == es.F64 else 12, 2: 24 if dt == es.F64 else 32}[kind]
     p = tmp_path / f"force_{dt}_{kind}_{tile}.json"
     p.write_text('{"segmented": [{"in_dtype": %d, "log2_segments": %d, "warps": %d, "kind": %d, '
                  '"tile": %d, "ms": -1}]}' % (dt, lg, warps, kind, tile))
