@@ -258,6 +258,34 @@ def test_config3_full():
         assert G.result_bits(r, o)[0] == oracle.exact_sum(b16, es.BF16, o, es.RNE, threads=16)
 
 
+def test_back_to_back_launches():
+    """Consecutive FP64 sums on one stream may overlap on the device: the next
+    launch starts streaming while the one before it merges and rounds, and
+    waits for it only before it touches the handle's partials, ticket and
+    result (programmatic dependent launch).  Sixteen different arrays (large
+    enough for the launches to overlap) are summed back to back with no
+    synchronisation in between, then eight of them are added back to back
+    into one accumulator; every result must equal the oracle's."""
+    arrays = []
+    for k in range(16):
+        n = (1 << 24) + 1001 * k
+        arrays.append(W.cancelling_f64(n, seed=100 + k) if k % 2 == 0 else W.uniform_f64(n, seed=100 + k))
+    xs = [G.to_device(b, es.F64, DEV, k % 3) for k, b in enumerate(arrays)]
+    torch.cuda.synchronize()
+    outs = [es.exact_sum(x, es.F64, es.RNE) for x in xs]
+    torch.cuda.synchronize()
+    for k, (b, r) in enumerate(zip(arrays, outs)):
+        assert G.result_bits(r, es.F64)[0] == oracle.exact_sum(b, es.F64, es.F64, es.RNE, threads=8), k
+    acc = es.new_accumulator(DEV)
+    for x in xs[:8]:
+        es.acc_add(acc, x)
+    r = es.acc_round(acc, es.F64, es.F64, es.RNE)
+    torch.cuda.synchronize()
+    want = oracle.exact_sum(np.concatenate(arrays[:8]), es.F64, es.F64, es.RNE, threads=8)
+    assert G.result_bits(r, es.F64)[0] == want
+    del xs
+
+
 def test_invalid_arguments():
     h = es.handle_for(0)
     x = torch.zeros(16, dtype=torch.float64, device=DEV)
