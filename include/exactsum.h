@@ -145,7 +145,13 @@ const char* exactsum_last_error(exactsum_t h);
 
 /* d_result (one element of out_dtype, device) <- round(sum of d_x[0..n)).
  * d_x: n elements of in_dtype in device memory (may be NULL when n == 0).
- * One kernel launch; no host synchronisation. */
+ * One kernel launch; no host synchronisation.  Results are stream-ordered
+ * as usual; on the device, an FP64 call may start streaming its input while
+ * the FP64 call just before it on the same stream (and handle) finishes its
+ * merge (programmatic dependent launch: it waits for that call before it
+ * touches the handle's workspace or its own result).  With any other stream
+ * operation in between (a copy, an event, another kernel) the calls are
+ * ordered as usual. */
 exactsum_status exactsum_sum(exactsum_t h, const void* d_x, int64_t n, exactsum_dtype in_dtype,
                              exactsum_dtype out_dtype, exactsum_round mode, void* d_result, exactsum_stream_t stream);
 
