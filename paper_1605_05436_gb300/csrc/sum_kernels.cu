@@ -85,6 +85,15 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
 #ifndef ES_PDL
 #define ES_PDL 1
 #endif
+// Vectors the last CTA of the TMA form gives up to the others.  Back to back,
+// the SM whose CTA merges and rounds frees up last, so the next launch's
+// last CTA (dispatched last) starts there about 8 us late; with that much
+// less to stream (about 19,000 vectors at the per-SM rate) it finishes with
+// the others.  With the launches serialised it is off the critical path.
+// (Back to back at 2^28: 0.3511 ms per launch against 0.3584; 38,912: 0.3500.)
+#ifndef ES_TAIL_CUT
+#define ES_TAIL_CUT 19456
+#endif
 
 // TMA-streaming form: one producer warp moves the CTA's range through a ring
 // of S shared-memory stages with bulk asynchronous copies (cp.async.bulk,
@@ -115,7 +124,15 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_tma(SumArgs a) {
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t G = gridDim.x;
+#if ES_TAIL_CUT > 0
+  // the last CTA takes ES_TAIL_CUT fewer vectors (at most a quarter of a
+  // share), the others share them
+  const int64_t cut = min((int64_t)ES_TAIL_CUT, a.nvec / (4 * G));
+  const int64_t vb = (a.nvec + cut) * blockIdx.x / G;
+  const int64_t ve = blockIdx.x == G - 1 ? a.nvec : (a.nvec + cut) * (blockIdx.x + 1) / G;
+#else
   const int64_t vb = a.nvec * blockIdx.x / G, ve = a.nvec * (blockIdx.x + 1) / G;
+#endif
   const int64_t nv_cta = ve - vb;
   const int64_t nbatch = (nv_cta + BATCH - 1) / BATCH;
   const uint4* vx = reinterpret_cast<const uint4*>((const char*)a.x + a.head * Geometry<DT>::ELEM_BYTES);
