@@ -210,8 +210,10 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
   __shared__ uint32_t blk_flags, is_last;
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  pdl_signal();
   const int64_t G = gridDim.x;
-  const int64_t vb = a.nvec * blockIdx.x / G, ve = a.nvec * (blockIdx.x + 1) / G;
+  int64_t vb, ve;
+  cta_range(a.nvec, vb, ve);
   const int64_t nv_cta = ve - vb;
   const int64_t nbatch = (nv_cta + BATCH - 1) / BATCH;
   const uint4* vx = reinterpret_cast<const uint4*>((const char*)a.x + a.head * 2);
@@ -346,9 +348,11 @@ __global__ void __launch_bounds__((C + 1) * 32, 1) sum_kernel_bf16t(SumArgs a) {
     if (lane == 0) wcol[32 * C + warp] = 0;
   }
   __syncthreads();
+  pdl_wait();
   finish_cta<BF16, C, NW, int64_t, true, (size_t)FDIG_DIGITS * FS * 4>(a, wcol, blk, limbs, blk_flags, &is_last);
 #else
   __syncthreads();
+  pdl_wait();
   finish_cta<BF16, FS, NW, int32_t, true>(a, reinterpret_cast<int32_t*>(fd), blk, limbs, blk_flags, &is_last);
 #endif
 }
@@ -367,8 +371,7 @@ static cudaError_t launch_sum_bf16t(const SumArgs& a, int max_ctas, cudaStream_t
   const int64_t want = (a.nvec + 2 * T - 1) / (2 * T);
   const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
   if (grid_out) *grid_out = grid;
-  sum_kernel_bf16t<C, U, S><<<grid, (C + 1) * 32, SMEM, stream>>>(a);
-  return cudaGetLastError();
+  return launch_single_array(sum_kernel_bf16t<C, U, S>, grid, (C + 1) * 32, SMEM, stream, a);
 }
 
 static cudaError_t launch_sum_bf16f(const SumArgs& a, int max_ctas, cudaStream_t stream, int* grid_out,

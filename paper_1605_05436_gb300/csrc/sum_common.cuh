@@ -22,6 +22,76 @@
 
 namespace es {
 
+// Programmatic dependent launch of the single-array kernels: a launch may start streaming
+// while the one before it on the stream merges and rounds (it waits for that
+// one before it touches the shared partials, ticket or result).  Only a
+// kernel that signals its dependents (this one) lets the next launch start
+// early; after any other stream operation the launch waits as usual.
+// (Back to back at 2^28: 0.3572 ms per launch against 0.3590 without.)
+#ifndef ES_PDL
+#define ES_PDL 1
+#endif
+// Vectors the last CTA of a single-array kernel gives up to the others.  Back to back,
+// the SM whose CTA merges and rounds frees up last, so the next launch's
+// last CTA (dispatched last) starts there about 8 us late; with that much
+// less to stream (about 19,000 vectors at the per-SM rate) it finishes with
+// the others.  With the launches serialised it is off the critical path.
+// (Back to back at 2^28: 0.3511 ms per launch against 0.3584; 38,912: 0.3500.)
+#ifndef ES_TAIL_CUT
+#define ES_TAIL_CUT 19456
+#endif
+
+// The two halves of programmatic dependent launch inside a kernel: let the
+// next launch on the stream start as this one's CTAs leave, and wait for the
+// launch before this one before touching the workspace it shared.
+__device__ __forceinline__ void pdl_signal() {
+#if ES_PDL
+  asm volatile("griddepcontrol.launch_dependents;");
+#endif
+}
+__device__ __forceinline__ void pdl_wait() {
+#if ES_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+// This CTA's vectors [vb, ve) of nvec: equal shares, except that the last
+// CTA gives up ES_TAIL_CUT vectors (at most a quarter of a share).
+__device__ __forceinline__ void cta_range(int64_t nvec, int64_t& vb, int64_t& ve) {
+  const int64_t G = gridDim.x;
+#if ES_TAIL_CUT > 0
+  const int64_t cut = min((int64_t)ES_TAIL_CUT, nvec / (4 * G));
+  vb = (nvec + cut) * blockIdx.x / G;
+  ve = blockIdx.x == G - 1 ? nvec : (nvec + cut) * (blockIdx.x + 1) / G;
+#else
+  vb = nvec * blockIdx.x / G;
+  ve = nvec * (blockIdx.x + 1) / G;
+#endif
+}
+
+// Launch a single-array kernel (with the programmatic-serialisation
+// attribute when ES_PDL is set).
+template <typename K>
+static inline cudaError_t launch_single_array(K kernel, int grid, int threads, size_t smem, cudaStream_t stream,
+                                              const SumArgs& a) {
+#if ES_PDL
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+#else
+  kernel<<<grid, threads, smem, stream>>>(a);
+  return cudaGetLastError();
+#endif
+}
+
 // Elements owned by thread t of CTA b: vectors vb + t + j*T (< ve), the
 // unaligned head (CTA 0) and the ragged tail (last CTA).
 template <int DT, int T>

@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   __shared__ uint32_t blk_flags, is_last;
 
   const int t = threadIdx.x;
+  pdl_signal();
   D* col = digits + t;
 #pragma unroll 4
   for (int i = 0; i < ND; ++i) col[i * T] = 0;
@@ -54,7 +55,8 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   uint32_t emax = 0;
   const uint4* vx = reinterpret_cast<const uint4*>((const char*)a.x + a.head * Geometry<DT>::ELEM_BYTES);
   const int64_t G = gridDim.x;
-  const int64_t vb = a.nvec * blockIdx.x / G, ve = a.nvec * (blockIdx.x + 1) / G;
+  int64_t vb, ve;
+  cta_range(a.nvec, vb, ve);
   int reg_left = REG_EVERY;
 
   // ---- hot loop: this thread's vectors vb + t + j*T, double buffered ----
@@ -73,27 +75,9 @@ __global__ void __launch_bounds__(T, 1) sum_kernel(SumArgs a) {
   __syncthreads();
   if (flags) atomicOr(&blk_flags, flags);
   __syncthreads();
+  pdl_wait();
   finish_cta<DT, T, NW, D>(a, digits, blk, limbs, blk_flags, &is_last);
 }
-
-// Programmatic dependent launch of the TMA form: a launch may start streaming
-// while the one before it on the stream merges and rounds (it waits for that
-// one before it touches the shared partials, ticket or result).  Only a
-// kernel that signals its dependents (this one) lets the next launch start
-// early; after any other stream operation the launch waits as usual.
-// (Back to back at 2^28: 0.3572 ms per launch against 0.3590 without.)
-#ifndef ES_PDL
-#define ES_PDL 1
-#endif
-// Vectors the last CTA of the TMA form gives up to the others.  Back to back,
-// the SM whose CTA merges and rounds frees up last, so the next launch's
-// last CTA (dispatched last) starts there about 8 us late; with that much
-// less to stream (about 19,000 vectors at the per-SM rate) it finishes with
-// the others.  With the launches serialised it is off the critical path.
-// (Back to back at 2^28: 0.3511 ms per launch against 0.3584; 38,912: 0.3500.)
-#ifndef ES_TAIL_CUT
-#define ES_TAIL_CUT 19456
-#endif
 
 // TMA-streaming form: one producer warp moves the CTA's range through a ring
 // of S shared-memory stages with bulk asynchronous copies (cp.async.bulk,
@@ -367,27 +351,10 @@ static cudaError_t launch_sum_t(const SumArgs& a, int max_ctas, cudaStream_t str
   const int64_t want = (a.nvec + 2 * COLS - 1) / (2 * COLS);
   const int grid = (int)(want < 1 ? 1 : (want > max_ctas ? max_ctas : want));
   if (grid_out) *grid_out = grid;
-  if constexpr (Cfg::TMA) {
-#if ES_PDL
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = SMEM;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const cudaError_t le = cudaLaunchKernelEx(&cfg, sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S, D>, a);
-    if (le != cudaSuccess) return le;
-#else
-    sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S, D><<<grid, THREADS, SMEM, stream>>>(a);
-#endif
-  }
+  if constexpr (Cfg::TMA)
+    return launch_single_array(sum_kernel_tma<DT, Cfg::C, Cfg::TU, Cfg::S, D>, grid, THREADS, SMEM, stream, a);
   else
-    sum_kernel<DT, Cfg::T, Cfg::U, D><<<grid, THREADS, SMEM, stream>>>(a);
-  return cudaGetLastError();
+    return launch_single_array(sum_kernel<DT, Cfg::T, Cfg::U, D>, grid, THREADS, SMEM, stream, a);
 }
 
 // Load and configure the single-array kernels of every input format now
